@@ -1,0 +1,170 @@
+/*
+ * msc.h -- C ABI of the GB300 (sm_103a) Morse-Smale segmentation and
+ * connected-components library (arXiv 2409.03771, "Distributed Path
+ * Compression for Piecewise Linear Morse-Smale Segmentations and Connected
+ * Components"), single GPU.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  - Pointers named d_* or documented as "device" are CUDA device pointers;
+ *    the caller owns every input, output and workspace buffer.  The library
+ *    allocates nothing on these calls.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ *    stream).  Calls only enqueue work: they are asynchronous on `stream`
+ *    and return before the GPU has finished.
+ *  - The return value reports host-side checks and launch errors:
+ *    MSC_OK, MSC_ERR_ARG (null pointer, bad size, bad connectivity),
+ *    MSC_ERR_WS (workspace smaller than msc_workspace_bytes), MSC_ERR_CUDA
+ *    (a CUDA call or launch failed).
+ *  - Errors found on the device are written to the caller's device status
+ *    word `d_status` (int32): the call first resets it to MSC_OK, then the
+ *    first error found wins (MSC_ERR_NAN, MSC_ERR_NOT_CONVERGED, MSC_ERR_ARG
+ *    for an out-of-range pointer or CSR column, MSC_ERR_INTERNAL).  Read it
+ *    after synchronising the stream.  Outputs are unspecified when it is
+ *    not MSC_OK.  No device error traps or hangs the GPU: every device loop
+ *    is bounded.
+ *  - Workspace: a device buffer of at least msc_workspace_bytes(op, n, nnz)
+ *    bytes, 256-byte aligned; its contents on entry do not matter and are
+ *    clobbered.
+ *  - Vertex ids of a regular grid are linear, x fastest:
+ *    v = x + nx * (y + ny * z).  Sizes are limited to n < 2^31 vertices.
+ *  - Outputs are deterministic: identical inputs give identical bytes.
+ */
+#ifndef MSC_H
+#define MSC_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#if defined(__GNUC__)
+#define MSC_API __attribute__((visibility("default")))
+#else
+#define MSC_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define MSC_OK 0
+#define MSC_ERR_ARG (-1)
+#define MSC_ERR_WS (-2)
+#define MSC_ERR_CUDA (-3)
+#define MSC_ERR_NAN (-4)
+#define MSC_ERR_NOT_CONVERGED (-5)
+#define MSC_ERR_BUDGET (-6)
+#define MSC_ERR_INTERNAL (-7)
+#define MSC_PENDING 1
+
+/* Regular grid: vertices per axis. */
+typedef struct {
+    int32_t nx, ny, nz;
+} msc_grid;
+
+/* Operation ids for msc_workspace_bytes. */
+enum {
+    MSC_OP_ORDER = 1,
+    MSC_OP_COMPRESS = 2,
+    MSC_OP_MS_ID = 3,
+    MSC_OP_SEGMENT = 4,
+    MSC_OP_CC_MASK = 5,
+    MSC_OP_CC_MESH = 6
+};
+
+/* Workspace bytes needed by `op` on n vertices (nnz CSR entries for
+ * MSC_OP_CC_MESH, ignored otherwise).  0 for an unknown op or bad size. */
+MSC_API size_t msc_workspace_bytes(int op, int64_t n, int64_t nnz);
+
+/* Human-readable name of a status code (static string). */
+MSC_API const char* msc_status_string(int code);
+
+/* Vertex order by Simulation of Simplicity (section "Preprocessing": sort
+ * the vertices by scalar value, break ties by global id, and give every
+ * vertex its index in the sorted array).
+ *   f       device float32[n]: the scalar field.  -0.0 ties with +0.0;
+ *           +-Inf are ordinary values; a NaN sets MSC_ERR_NAN.
+ *   order   device int32[n] out: order[v] = #{u : (f[u], u) < (f[v], v)},
+ *           a permutation of 0..n-1.
+ * Method: LSD radix sort (four 8-bit digits) of order-preserving uint32
+ * keys with a vertex-id payload, stable, ending in order[id] = position. */
+MSC_API int msc_order(const float* f, int64_t n, int32_t* order, void* ws, size_t ws_bytes,
+              int32_t* d_status, void* stream);
+
+/* Steepest-descent and steepest-ascent pointers on the implicit Freudenthal
+ * triangulation of a regular grid (Alg. 1 initialisation: every vertex
+ * points at its largest neighbour; section "Ascending and Descending
+ * Manifolds").  The link of a vertex holds the 14 neighbours at offsets
+ * +-(1,0,0), +-(0,1,0), +-(0,0,1), +-(1,1,0), +-(1,0,1), +-(0,1,1),
+ * +-(1,1,1) that lie inside the grid.
+ *   order     device int32[n], a permutation of 0..n-1 (msc_order output).
+ *   asc_ptr   device int32[n] out: the neighbour of smallest order, or v
+ *             itself when v is a minimum.
+ *   desc_ptr  device int32[n] out: the neighbour of largest order, or v
+ *             itself when v is a maximum.
+ * No workspace; no device-detected errors (order must be a permutation). */
+MSC_API int msc_steepest_grid(const int32_t* order, msc_grid g, int32_t* asc_ptr, int32_t* desc_ptr,
+                      void* stream);
+
+/* The same over an explicit adjacency (the explicit-triangulation case):
+ *   row  device int32[n+1], col device int32[row[n]]: CSR of a symmetric
+ *        vertex adjacency; row[0] = 0.  A column outside [0, n) sets
+ *        MSC_ERR_ARG in d_status. */
+MSC_API int msc_steepest_csr(const int32_t* order, const int32_t* row, const int32_t* col, int32_t n,
+                     int32_t* asc_ptr, int32_t* desc_ptr, int32_t* d_status, void* stream);
+
+/* Path compression by pointer jumping, in place (Alg. 1 compression loop:
+ * d[v] <- d[d[v]] until d[d[v]] = d[v]).  On return every active entry
+ * holds the fixed point at the end of its pointer path.
+ *   ptr  device int32[n], in/out.  Negative entries are inactive (the
+ *        paper's -1 outside a feature mask) and are left as they are.
+ *        An active entry pointing outside [0, n) or at an inactive entry
+ *        sets MSC_ERR_ARG; a pointer cycle sets MSC_ERR_NOT_CONVERGED
+ *        after ceil(log2 n) + 2 sweeps. */
+MSC_API int msc_compress(int32_t* ptr, int32_t n, void* ws, size_t ws_bytes, int32_t* d_status,
+                 void* stream);
+
+/* Dense Morse-Smale cell ids (section "Ascending and Descending
+ * Segmentation": vertices whose steepest descent and ascent end in the
+ * same (minimum, maximum) pair form one cell).
+ *   asc, desc  device int32[n]: per-vertex minimum and maximum labels,
+ *              each in [0, n).
+ *   ms         device int32[n] out: the index of (asc[v], desc[v]) among
+ *              the distinct pairs sorted lexicographically, asc first.
+ *   num_cells  device int32 out: the number of distinct pairs. */
+MSC_API int msc_ms_id(const int32_t* asc, const int32_t* desc, int32_t n, int32_t* ms,
+              int32_t* num_cells, void* ws, size_t ws_bytes, int32_t* d_status, void* stream);
+
+/* The whole segmentation of a grid field: msc_order, steepest pointers,
+ * path compression of both, Morse-Smale ids.  Outputs (device, n each):
+ * order, asc (minimum label), desc (maximum label), ms; num_cells (device
+ * int32).  Workspace: msc_workspace_bytes(MSC_OP_SEGMENT, n, 0). */
+MSC_API int msc_segment(const float* f, msc_grid g, int32_t* order, int32_t* asc, int32_t* desc,
+                int32_t* ms, int32_t* num_cells, void* ws, size_t ws_bytes, int32_t* d_status,
+                void* stream);
+
+/* Connected components of a feature mask on a regular grid (Alg. 3,
+ * implicitly thresholded grid: label -1 off the mask).
+ *   mask   device uint8[n]: nonzero = feature vertex.
+ *   conn   6 (face neighbours) or 14 (the Freudenthal link).
+ *   label  device int32[n] out: the smallest vertex id of the component
+ *          (the paper labels with the largest; the partition is the same),
+ *          -1 where mask is zero.
+ * Method: union-find with min-label hooking, tile-local in shared memory,
+ * then across tile faces, then pointer jumping to the roots. */
+MSC_API int msc_cc_mask(const uint8_t* mask, msc_grid g, int32_t conn, int32_t* label, void* ws,
+                size_t ws_bytes, int32_t* d_status, void* stream);
+
+/* Connected components of an explicit mesh given as its vertex adjacency
+ * (the explicit-CC variant of the Experiments section).
+ *   row, col  device int32 CSR (row[n+1], col[row[n]]), symmetric.
+ *   label     device int32[n] out: smallest vertex id of the component; a
+ *             vertex with no edge labels itself.
+ * A column outside [0, n) sets MSC_ERR_ARG in d_status. */
+MSC_API int msc_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* label, void* ws,
+                size_t ws_bytes, int32_t* d_status, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* MSC_H */

@@ -1,0 +1,300 @@
+"""Python binding of libmsc (include/msc.h): Morse-Smale segmentation and
+connected components by path compression on one GB300 GPU.
+
+Two layers, both argument marshalling only -- every step runs in the CUDA
+kernels of libmsc.so:
+
+* ``msc_*`` functions mirror the C ABI one to one: torch CUDA tensors in,
+  raw device pointers and the current torch stream passed down, the C
+  status code returned.
+* ``order``, ``steepest_grid``, ``steepest_csr``, ``compress``, ``ms_id``,
+  ``segment``, ``cc_mask``, ``cc_mesh`` allocate outputs and workspace with
+  torch on the input's device, call the C ABI, synchronise and raise
+  ``MSCError`` on any host or device error.
+
+There is no CPU fallback: if libmsc.so is missing or no CUDA device is
+present, every call raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from . import _build
+
+__all__ = [
+    "MSCError", "load", "lib_path",
+    "msc_workspace_bytes", "msc_status_string", "msc_order", "msc_steepest_grid", "msc_steepest_csr",
+    "msc_compress", "msc_ms_id", "msc_segment", "msc_cc_mask", "msc_cc_mesh",
+    "order", "steepest_grid", "steepest_csr", "compress", "ms_id", "segment", "cc_mask", "cc_mesh",
+    "OP_ORDER", "OP_COMPRESS", "OP_MS_ID", "OP_SEGMENT", "OP_CC_MASK", "OP_CC_MESH",
+]
+
+OK, ERR_ARG, ERR_WS, ERR_CUDA, ERR_NAN, ERR_NOT_CONVERGED, ERR_BUDGET, ERR_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
+PENDING = 1
+OP_ORDER, OP_COMPRESS, OP_MS_ID, OP_SEGMENT, OP_CC_MASK, OP_CC_MESH = 1, 2, 3, 4, 5, 6
+
+
+class MSCError(RuntimeError):
+    def __init__(self, code: int, where: str):
+        super().__init__(f"{where}: {msc_status_string(code)} ({code})")
+        self.code = code
+
+
+class Grid(ctypes.Structure):
+    _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+_lib = None
+
+
+def lib_path() -> str:
+    return _build.LIB
+
+
+def load(build_if_missing: bool = False):
+    """Load libmsc.so (raises if it is not built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(_build.LIB):
+        if not build_if_missing:
+            raise RuntimeError(f"libmsc.so is not built ({_build.LIB}); run __graft_entry__.build()")
+        _build.build()
+    lib = ctypes.CDLL(_build.LIB)
+    P, I32, I64, SZ = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64, ctypes.c_size_t
+    sig = {
+        "msc_workspace_bytes": (SZ, [ctypes.c_int, I64, I64]),
+        "msc_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+        "msc_order": (ctypes.c_int, [P, I64, P, P, SZ, P, P]),
+        "msc_steepest_grid": (ctypes.c_int, [P, Grid, P, P, P]),
+        "msc_steepest_csr": (ctypes.c_int, [P, P, P, I32, P, P, P, P]),
+        "msc_compress": (ctypes.c_int, [P, I32, P, SZ, P, P]),
+        "msc_ms_id": (ctypes.c_int, [P, P, I32, P, P, P, SZ, P, P]),
+        "msc_segment": (ctypes.c_int, [P, Grid, P, P, P, P, P, P, SZ, P, P]),
+        "msc_cc_mask": (ctypes.c_int, [P, Grid, I32, P, P, SZ, P, P]),
+        "msc_cc_mesh": (ctypes.c_int, [P, P, I32, P, P, SZ, P, P]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+# ---------------------------------------------------------------------------
+# C ABI mirror
+
+
+def _p(t) -> int:
+    if t is None:
+        return 0
+    if isinstance(t, int):
+        return t
+    return t.data_ptr()
+
+
+def _stream(stream) -> int:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(stream, int):
+        return stream
+    return stream.cuda_stream
+
+
+def _grid(dims) -> Grid:
+    nx, ny, nz = (int(d) for d in dims)
+    return Grid(nx, ny, nz)
+
+
+def msc_workspace_bytes(op: int, n: int, nnz: int = 0) -> int:
+    return int(load().msc_workspace_bytes(op, n, nnz))
+
+
+def msc_status_string(code: int) -> str:
+    try:
+        return load().msc_status_string(code).decode()
+    except Exception:  # library not loadable: still describe the code
+        return str(code)
+
+
+def msc_order(f, n, order, ws, ws_bytes, status, stream=None) -> int:
+    return load().msc_order(_p(f), n, _p(order), _p(ws), ws_bytes, _p(status), _stream(stream))
+
+
+def msc_steepest_grid(order, dims, asc_ptr, desc_ptr, stream=None) -> int:
+    return load().msc_steepest_grid(_p(order), _grid(dims), _p(asc_ptr), _p(desc_ptr), _stream(stream))
+
+
+def msc_steepest_csr(order, row, col, n, asc_ptr, desc_ptr, status, stream=None) -> int:
+    return load().msc_steepest_csr(_p(order), _p(row), _p(col), n, _p(asc_ptr), _p(desc_ptr), _p(status),
+                                   _stream(stream))
+
+
+def msc_compress(ptr, n, ws, ws_bytes, status, stream=None) -> int:
+    return load().msc_compress(_p(ptr), n, _p(ws), ws_bytes, _p(status), _stream(stream))
+
+
+def msc_ms_id(asc, desc, n, ms, num_cells, ws, ws_bytes, status, stream=None) -> int:
+    return load().msc_ms_id(_p(asc), _p(desc), n, _p(ms), _p(num_cells), _p(ws), ws_bytes, _p(status),
+                            _stream(stream))
+
+
+def msc_segment(f, dims, order, asc, desc, ms, num_cells, ws, ws_bytes, status, stream=None) -> int:
+    return load().msc_segment(_p(f), _grid(dims), _p(order), _p(asc), _p(desc), _p(ms), _p(num_cells),
+                              _p(ws), ws_bytes, _p(status), _stream(stream))
+
+
+def msc_cc_mask(mask, dims, conn, label, ws, ws_bytes, status, stream=None) -> int:
+    return load().msc_cc_mask(_p(mask), _grid(dims), conn, _p(label), _p(ws), ws_bytes, _p(status),
+                              _stream(stream))
+
+
+def msc_cc_mesh(row, col, n, label, ws, ws_bytes, status, stream=None) -> int:
+    return load().msc_cc_mesh(_p(row), _p(col), n, _p(label), _p(ws), ws_bytes, _p(status), _stream(stream))
+
+
+# ---------------------------------------------------------------------------
+# convenience layer
+
+
+def _dev(t: torch.Tensor) -> torch.device:
+    if not t.is_cuda:
+        raise MSCError(ERR_ARG, "input must be a CUDA tensor (there is no CPU path)")
+    return t.device
+
+
+def _check(code: int, where: str):
+    if code != OK:
+        raise MSCError(code, where)
+
+
+def _finish(status: torch.Tensor, where: str):
+    code = int(status.item())  # synchronises the stream
+    _check(code, where)
+
+
+def _ws(op: int, n: int, dev, nnz: int = 0) -> torch.Tensor:
+    return torch.empty(max(msc_workspace_bytes(op, n, nnz), 1), dtype=torch.uint8, device=dev)
+
+
+def _flat(t: torch.Tensor, dtype) -> torch.Tensor:
+    if t.dtype != dtype:
+        raise MSCError(ERR_ARG, f"expected {dtype}, got {t.dtype}")
+    return t.contiguous().view(-1)
+
+
+def _cols(col: torch.Tensor) -> torch.Tensor:
+    """CSR columns; an edgeless graph still gets a valid (unread) pointer."""
+    col = _flat(col, torch.int32)
+    return col if col.numel() else torch.zeros(1, dtype=torch.int32, device=col.device)
+
+
+def order(f: torch.Tensor) -> torch.Tensor:
+    dev = _dev(f)
+    f = _flat(f, torch.float32)
+    n = f.numel()
+    out = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = _ws(OP_ORDER, n, dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(msc_order(f, n, out, ws, ws.numel(), st), "msc_order")
+    _finish(st, "msc_order")
+    return out
+
+
+def steepest_grid(order_field: torch.Tensor, dims):
+    dev = _dev(order_field)
+    o = _flat(order_field, torch.int32)
+    asc = torch.empty_like(o)
+    desc = torch.empty_like(o)
+    _check(msc_steepest_grid(o, dims, asc, desc), "msc_steepest_grid")
+    torch.cuda.current_stream(dev).synchronize()
+    return asc, desc
+
+
+def steepest_csr(order_field: torch.Tensor, row: torch.Tensor, col: torch.Tensor):
+    dev = _dev(order_field)
+    o = _flat(order_field, torch.int32)
+    row = _flat(row, torch.int32)
+    col = _cols(col)
+    n = row.numel() - 1
+    asc = torch.empty(n, dtype=torch.int32, device=dev)
+    desc = torch.empty(n, dtype=torch.int32, device=dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(msc_steepest_csr(o, row, col, n, asc, desc, st), "msc_steepest_csr")
+    _finish(st, "msc_steepest_csr")
+    return asc, desc
+
+
+def compress(ptr: torch.Tensor, inplace: bool = False) -> torch.Tensor:
+    dev = _dev(ptr)
+    p = _flat(ptr, torch.int32)
+    if not inplace:
+        p = p.clone()
+    n = p.numel()
+    ws = _ws(OP_COMPRESS, n, dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(msc_compress(p, n, ws, ws.numel(), st), "msc_compress")
+    _finish(st, "msc_compress")
+    return p
+
+
+def ms_id(asc: torch.Tensor, desc: torch.Tensor):
+    dev = _dev(asc)
+    a = _flat(asc, torch.int32)
+    d = _flat(desc, torch.int32)
+    n = a.numel()
+    ms = torch.empty(n, dtype=torch.int32, device=dev)
+    k = torch.empty(1, dtype=torch.int32, device=dev)
+    ws = _ws(OP_MS_ID, n, dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(msc_ms_id(a, d, n, ms, k, ws, ws.numel(), st), "msc_ms_id")
+    _finish(st, "msc_ms_id")
+    return ms, int(k.item())
+
+
+def segment(f: torch.Tensor, dims, ws: torch.Tensor | None = None):
+    """order, asc (minimum label), desc (maximum label), ms, num_cells."""
+    dev = _dev(f)
+    f = _flat(f, torch.float32)
+    n = f.numel()
+    if n != int(dims[0]) * int(dims[1]) * int(dims[2]):
+        raise MSCError(ERR_ARG, "segment: dims do not match the field size")
+    outs = [torch.empty(n, dtype=torch.int32, device=dev) for _ in range(4)]
+    k = torch.empty(1, dtype=torch.int32, device=dev)
+    if ws is None:
+        ws = _ws(OP_SEGMENT, n, dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(msc_segment(f, dims, *outs, k, ws, ws.numel(), st), "msc_segment")
+    _finish(st, "msc_segment")
+    return (*outs, int(k.item()))
+
+
+def cc_mask(mask: torch.Tensor, dims, conn: int = 6) -> torch.Tensor:
+    dev = _dev(mask)
+    m = _flat(mask, torch.uint8)
+    n = m.numel()
+    if n != int(dims[0]) * int(dims[1]) * int(dims[2]):
+        raise MSCError(ERR_ARG, "cc_mask: dims do not match the mask size")
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = _ws(OP_CC_MASK, n, dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(msc_cc_mask(m, dims, conn, lab, ws, ws.numel(), st), "msc_cc_mask")
+    _finish(st, "msc_cc_mask")
+    return lab
+
+
+def cc_mesh(row: torch.Tensor, col: torch.Tensor) -> torch.Tensor:
+    dev = _dev(row)
+    row = _flat(row, torch.int32)
+    col = _cols(col)
+    n = row.numel() - 1
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = _ws(OP_CC_MESH, n, dev, col.numel())
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    _check(msc_cc_mesh(row, col, n, lab, ws, ws.numel(), st), "msc_cc_mesh")
+    _finish(st, "msc_cc_mesh")
+    return lab

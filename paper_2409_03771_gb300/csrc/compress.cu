@@ -1,0 +1,216 @@
+// Path compression by pointer doubling (Alg. 1 compression loop): every
+// active vertex v does u <- d[v], w <- d[u]; if u = w it is finished,
+// otherwise d[v] <- w.  As in the paper the update is in place: a read of
+// d[u] may already see this sweep's write, which only lengthens the jump,
+// so ceil(log2 L) + 1 sweeps finish a longest path of L vertices.
+//
+// GPU form: one launch per sweep over all vertices (int4 loads, four
+// vertices per thread), launched ceil(log2 n) + 2 times.  Each sweep counts
+// the vertices it changed; a sweep whose predecessor changed nothing
+// returns at once, so no host synchronisation is needed.  Once at most
+// n >> build_shift vertices changed, the sweep also appends the changed
+// vertices to an active list (block-aggregated atomics) and the following
+// sweeps walk only that list -- the GPU counterpart of the paper's
+// per-thread active lists.  A change in the last sweep means a pointer
+// cycle: MSC_ERR_NOT_CONVERGED.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "compress.cuh"
+
+namespace msc {
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kChunk = kThreads * 4;
+
+struct JumpArray {
+    int32_t* p;
+    JumpCtl* ctl;
+    int32_t* list0;
+    int32_t* list1;
+};
+
+struct JumpPair {
+    JumpArray a[2];
+    int32_t n;
+    int vec;  // int4 access allowed
+};
+
+// One jump of one vertex; returns true when d changed.
+__device__ __forceinline__ bool jump_one(const int32_t* p, int32_t n, int32_t& d, int32_t* status) {
+    const int32_t u = d;
+    if (u < 0) return false;
+    if ((uint32_t)u >= (uint32_t)n) {
+        record_error(status, MSC_ERR_ARG);
+        return false;
+    }
+    const int32_t w = p[u];
+    if (w == u) return false;
+    if (w < 0) {
+        record_error(status, MSC_ERR_ARG);
+        return false;
+    }
+    d = w;
+    return true;
+}
+
+__global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, int build_shift,
+                                                   int32_t* status) {
+    const JumpArray A = pr.a[blockIdx.y];
+    const int32_t n = pr.n;
+    int32_t* p = A.p;
+    const uint32_t prev = step == 0 ? (uint32_t)n : A.ctl->cnt[step - 1];
+    if (prev == 0) return;
+    const bool from_list = step > 0 && A.ctl->built[step - 1] != 0;
+    const bool build = prev <= ((uint32_t)n >> build_shift);
+    if (build && blockIdx.x == 0 && threadIdx.x == 0) A.ctl->built[step] = 1u;
+    int32_t* out_list = (step & 1) ? A.list1 : A.list0;
+    const int32_t* in_list = (step & 1) ? A.list0 : A.list1;
+
+    __shared__ uint32_t s_warp[kThreads / 32];
+    __shared__ uint32_t s_base;
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t total = from_list ? (int64_t)prev : (int64_t)n;
+    const int64_t nchunks = (total + kChunk - 1) / kChunk;
+    uint32_t changed_total = 0;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
+        int32_t vid[4];
+        uint32_t ch = 0;
+        if (!from_list) {
+            const int64_t v0 = c * kChunk + (int64_t)tid * 4;
+            if (pr.vec && v0 + 3 < n) {
+                int4 d = *reinterpret_cast<const int4*>(p + v0);
+                ch |= jump_one(p, n, d.x, status) ? 1u : 0u;
+                ch |= jump_one(p, n, d.y, status) ? 2u : 0u;
+                ch |= jump_one(p, n, d.z, status) ? 4u : 0u;
+                ch |= jump_one(p, n, d.w, status) ? 8u : 0u;
+                if (ch) *reinterpret_cast<int4*>(p + v0) = d;
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j) {
+                    if (v0 + j < n) {
+                        int32_t d = p[v0 + j];
+                        if (jump_one(p, n, d, status)) {
+                            p[v0 + j] = d;
+                            ch |= 1u << j;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < 4; ++j) vid[j] = (int32_t)(v0 + j);
+        } else {
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int64_t i = c * kChunk + (int64_t)j * kThreads + tid;
+                vid[j] = -1;
+                if (i < total) {
+                    const int32_t v = in_list[i];
+                    vid[j] = v;
+                    MSC_GUARD((uint32_t)v < (uint32_t)n, status, -121) {}
+#ifdef MSC_DEBUG_BOUNDS
+                    if ((uint32_t)v >= (uint32_t)n) continue;
+#endif
+                    int32_t d = p[v];
+                    if (jump_one(p, n, d, status)) {
+                        p[v] = d;
+                        ch |= 1u << j;
+                    }
+                }
+            }
+        }
+        const uint32_t cnt = __popc(ch);
+        changed_total += cnt;
+        if (build) {  // append the changed vertices; trip count is block-uniform
+            uint32_t incl = cnt;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+                if (lane >= o) incl += t;
+            }
+            if (lane == 31) s_warp[warp] = incl;
+            __syncthreads();
+            if (tid == 0) {
+                uint32_t run = 0;
+                for (int w = 0; w < kThreads / 32; ++w) {
+                    const uint32_t t = s_warp[w];
+                    s_warp[w] = run;
+                    run += t;
+                }
+                s_base = run ? atomicAdd(&A.ctl->cnt[step], run) : 0u;
+            }
+            __syncthreads();
+            uint32_t off = s_base + s_warp[warp] + incl - cnt;
+#pragma unroll
+            for (int j = 0; j < 4; ++j)
+                if (ch & (1u << j)) {
+                    MSC_GUARD(off < (uint32_t)n / 2 + 1, status, -122)
+                    out_list[off] = vid[j];
+                    ++off;
+                }
+            __syncthreads();
+        }
+    }
+    if (!build) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) changed_total += __shfl_xor_sync(0xffffffffu, changed_total, o);
+        if (lane == 0 && changed_total) atomicAdd(&A.ctl->cnt[step], changed_total);
+    }
+}
+
+__global__ void k_jump_finish(const JumpPair pr, int count, int last, int32_t* status) {
+    for (int i = 0; i < count; ++i)
+        if (pr.a[i].ctl->cnt[last] != 0u) record_error(status, MSC_ERR_NOT_CONVERGED);
+}
+
+}  // namespace
+
+int compress_steps(int64_t n) { return std::min(kMaxJumpSteps, ceil_log2(std::max<int64_t>(n, 2)) + 2); }
+
+static int64_t list_capacity(int64_t n) { return n / 2 + 1; }
+
+void size_compress_scratch(Sizer& s, int64_t n, int count) {
+    s.take<JumpCtl>(count);
+    s.take<int32_t>((size_t)count * 2 * list_capacity(n));
+}
+
+CompressScratch carve_compress_scratch(Carver& c, int64_t n, int count) {
+    CompressScratch sc;
+    sc.ctl = c.take<JumpCtl>(count);
+    sc.list_cap = list_capacity(n);
+    sc.lists = c.take<int32_t>((size_t)count * 2 * sc.list_cap);
+    return sc;
+}
+
+int run_compress(int32_t* const* ptrs, int count, int32_t n, const CompressScratch& sc,
+                 int32_t* status, cudaStream_t s, const CompressTune& tune) {
+    if (n <= 0 || count < 1 || count > 2) return n < 0 ? MSC_ERR_ARG : MSC_OK;
+    MSC_TRY(cudaMemsetAsync(sc.ctl, 0, sizeof(JumpCtl) * count, s));
+    JumpPair pr{};
+    pr.n = n;
+    pr.vec = 1;
+    for (int i = 0; i < count; ++i) {
+        pr.a[i].p = ptrs[i];
+        pr.a[i].ctl = sc.ctl + i;
+        pr.a[i].list0 = sc.lists + (size_t)i * 2 * sc.list_cap;
+        pr.a[i].list1 = pr.a[i].list0 + sc.list_cap;
+        if ((uintptr_t)ptrs[i] % 16 != 0) pr.vec = 0;
+    }
+    const int build_shift = std::max(1, std::min(tune.build_shift, 30));
+    int occ = 1;
+    MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jump, kThreads, 0));
+    const int64_t chunks = ceil_div(n, kChunk);
+    const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)current_device().sms * std::max(occ, 1)));
+    const int steps = compress_steps(n);
+    for (int st = 0; st < steps; ++st) {
+        k_jump<<<dim3(gx, count), kThreads, 0, s>>>(pr, st, build_shift, status);
+        MSC_LAUNCHED();
+    }
+    k_jump_finish<<<1, 1, 0, s>>>(pr, count, steps - 1, status);
+    MSC_LAUNCHED();
+    return MSC_OK;
+}
+
+}  // namespace msc

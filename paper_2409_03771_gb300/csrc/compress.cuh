@@ -1,0 +1,39 @@
+// Path compression by pointer jumping (in place), with device-side
+// convergence detection and active-list compaction.
+#pragma once
+
+#include "common.cuh"
+
+namespace msc {
+
+constexpr int kMaxJumpSteps = 64;
+
+// Per pointer array; zeroed at the start of every compression.
+struct JumpCtl {
+    uint32_t cnt[kMaxJumpSteps];    // vertices changed in each step
+    uint32_t built[kMaxJumpSteps];  // step wrote its changed vertices to a list
+};
+
+struct CompressTune {
+    int build_shift = 3;  // build the active list once <= n >> build_shift changed
+};
+
+// Sweeps launched for n vertices: ceil(log2 n) + 2 (enough for any forest;
+// more are needed only by a pointer cycle).
+int compress_steps(int64_t n);
+
+// Workspace pieces for `count` arrays of n entries.
+void size_compress_scratch(Sizer& s, int64_t n, int count);
+struct CompressScratch {
+    JumpCtl* ctl;     // [count]
+    int32_t* lists;   // [count][2][list_cap]
+    int64_t list_cap;
+};
+CompressScratch carve_compress_scratch(Carver& c, int64_t n, int count);
+
+// Compress `count` (1 or 2) arrays of n entries in place.  Negative entries
+// are inactive.  Errors go to status (MSC_ERR_ARG, MSC_ERR_NOT_CONVERGED).
+int run_compress(int32_t* const* ptrs, int count, int32_t n, const CompressScratch& sc,
+                 int32_t* status, cudaStream_t s, const CompressTune& tune = CompressTune());
+
+}  // namespace msc

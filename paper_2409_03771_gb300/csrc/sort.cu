@@ -1,0 +1,438 @@
+// Onesweep LSD radix sort for the vertex order (Simulation of Simplicity,
+// section "Preprocessing": sort by value, ties by global id).
+//
+// Keys: float32 bits mapped to an order-preserving uint32 (-0.0 first
+// folded onto +0.0 so that the two tie, as IEEE '<' says).  Four 8-bit
+// digit passes, least significant first; every pass is stable, and the
+// first pass reads the vertices in id order, so equal keys stay in id
+// order: the final position of v is its rank under (f[v], v).
+//
+// One pass = one kernel.  A block takes tiles of 4096 keys from a global
+// atomic counter (so every predecessor tile is owned by a running block),
+// ranks its keys per digit with warp match-any, publishes its per-digit
+// counts to a decoupled look-back array, sums its predecessors' counts and
+// scatters.  The last pass writes order[id] = position directly.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <utility>
+
+#include "sort.cuh"
+
+namespace msc {
+#ifdef MSC_DEBUG_BOUNDS
+__device__ uint32_t g_sort_dbg[16];
+#endif
+namespace {
+
+constexpr int kThreads = 256;
+constexpr int kItems = kSortTile / kThreads;  // 16
+constexpr int kWarps = kThreads / kWarp;      // 8
+constexpr int kBins = 256;
+constexpr unsigned long long kFlagAgg = 1ull << 62;
+constexpr unsigned long long kFlagInc = 2ull << 62;
+constexpr uint32_t kSpinLimit = 1u << 22;
+
+__device__ __forceinline__ uint32_t float_key(float x) {
+    uint32_t u = __float_as_uint(x);
+    if (u == 0x80000000u) u = 0u;  // -0.0 ties with +0.0
+    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+}
+
+__device__ __forceinline__ bool is_nan_bits(float x) {
+    return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u;
+}
+
+// Inclusive scan over 256 values held one per thread (kThreads == 256).
+__device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t* s_w) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
+        if (lane >= o) v += t;
+    }
+    if (lane == 31) s_w[warp] = v;
+    __syncthreads();
+    if (warp == 0) {
+        uint32_t t = lane < kWarps ? s_w[lane] : 0u;
+#pragma unroll
+        for (int o = 1; o < kWarps; o <<= 1) {
+            const uint32_t q = __shfl_up_sync(0xffffffffu, t, o);
+            if (lane >= o) t += q;
+        }
+        if (lane < kWarps) s_w[lane] = t;
+    }
+    __syncthreads();
+    if (warp > 0) v += s_w[warp - 1];
+    __syncthreads();
+    return v;
+}
+
+// Digit histograms for `npass` passes over n keys (keys read from `keys`,
+// or made from the float field `f`).
+template <typename KeyT, bool FROM_F>
+__global__ void __launch_bounds__(256) k_hist(const KeyT* __restrict__ keys,
+                                              const float* __restrict__ f, int64_t n_host,
+                                              const int32_t* __restrict__ d_n, int npass,
+                                              uint32_t* __restrict__ hist, int32_t* status) {
+    __shared__ uint32_t sh[8 * kBins];
+    for (int i = threadIdx.x; i < 8 * kBins; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    const int64_t n = d_n ? (int64_t)*d_n : n_host;
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    bool saw_nan = false;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < n; i += stride) {
+        const bool valid = i < n;
+        KeyT k = 0;
+        if (valid) {
+            if constexpr (FROM_F) {
+                const float x = f[i];
+                saw_nan |= is_nan_bits(x);
+                k = float_key(x);
+            } else {
+                k = keys[i];
+            }
+        }
+        for (int p = 0; p < npass; ++p) {
+            const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh[p * kBins + d], __popc(peers));
+        }
+    }
+    if (saw_nan) record_error(status, MSC_ERR_NAN);
+    __syncthreads();
+    for (int i = threadIdx.x; i < npass * kBins; i += blockDim.x)
+        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+}
+
+template <typename KeyT>
+struct PassArgs {
+    const KeyT* keys_in;
+    const float* f_in;
+    const int32_t* vals_in;
+    KeyT* keys_out;
+    int32_t* vals_out;
+    int32_t* order_out;
+    int64_t n;
+    const int32_t* d_n;
+    const uint32_t* hist;  // this pass's 256 counts
+    int shift;
+    unsigned long long* lookback;
+    uint32_t* tile_counter;
+    uint32_t epoch;
+    int32_t* status;
+};
+
+template <typename KeyT, bool STAGE>
+constexpr size_t pass_smem_bytes() {
+    return (size_t)(kWarps * kBins + 4 * kBins + 32) * 4 +
+           (STAGE ? (size_t)kSortTile * (sizeof(KeyT) + 4) : 0);
+}
+
+// One onesweep digit pass.  FROM_F: keys come from the float field and
+// the payload is the vertex id.  TO_ORDER: write order[payload] = position
+// instead of the sorted (key, payload) arrays.
+template <typename KeyT, bool FROM_F, bool TO_ORDER>
+__global__ void __launch_bounds__(kThreads) k_onesweep(const PassArgs<KeyT> a) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem);  // [kWarps][256]
+    uint32_t* s_total = s_whist + kWarps * kBins;          // [256]
+    uint32_t* s_excl = s_total + kBins;                    // [256] tile-local bin starts
+    uint32_t* s_gbase = s_excl + kBins;                    // [256] global base of the bin
+    uint32_t* s_bstart = s_gbase + kBins;                  // [256] global bin starts
+    uint32_t* s_misc = s_bstart + kBins;                   // [0] tile id, [1..8] scan
+    KeyT* s_keys = reinterpret_cast<KeyT*>(s_misc + 32);
+    int32_t* s_vals = reinterpret_cast<int32_t*>(s_keys + kSortTile);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int64_t n = a.d_n ? (int64_t)*a.d_n : a.n;
+    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
+    {
+        const uint32_t c = a.hist[tid];
+        s_bstart[tid] = block_scan_256(c, s_misc + 1) - c;
+    }
+    for (;;) {
+        if (tid == 0) s_misc[0] = atomicAdd(a.tile_counter, 1u);
+        for (int i = tid; i < kWarps * kBins; i += kThreads) s_whist[i] = 0;
+        __syncthreads();
+        const int64_t tile = s_misc[0];
+        if (tile >= ntiles) break;
+        const int64_t base = tile * kSortTile + warp * (kItems * 32);
+
+        KeyT key[kItems];
+        int32_t val[kItems];
+        uint32_t rk[kItems];  // (digit << 16) | rank among the warp's equal digits
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const int64_t idx = base + k * 32 + lane;
+            if (idx < n) {
+                if constexpr (FROM_F) {
+                    key[k] = (KeyT)float_key(a.f_in[idx]);
+                    val[k] = (int32_t)idx;
+                } else {
+                    key[k] = a.keys_in[idx];
+                    val[k] = a.vals_in[idx];
+                }
+            } else {
+                key[k] = 0;
+                val[k] = -1;
+            }
+        }
+        uint32_t* wh = s_whist + warp * kBins;
+#pragma unroll
+        for (int k = 0; k < kItems; ++k) {
+            const bool valid = base + k * 32 + lane < n;
+            const uint32_t d = valid ? (uint32_t)(key[k] >> a.shift) & 255u : 256u;
+            const uint32_t peers = __match_any_sync(0xffffffffu, d);
+            const int leader = __ffs(peers) - 1;
+            uint32_t before = 0;
+            if (lane == leader && valid) {
+                before = wh[d];
+                wh[d] = before + __popc(peers);
+            }
+            before = __shfl_sync(0xffffffffu, before, leader);
+            rk[k] = (d << 16) | (before + __popc(peers & lanemask_lt()));
+            __syncwarp();
+        }
+        __syncthreads();
+#ifdef MSC_DEBUG_BOUNDS
+        {   // each warp's histogram must hold exactly its valid items
+            uint32_t sum = 0;
+            for (int i = lane; i < kBins; i += 32) sum += wh[i];
+            for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+            const int64_t wv = min((int64_t)(kItems * 32), max((int64_t)0, n - base));
+            if (lane == 0 && sum != (uint32_t)wv && atomicCAS(&g_sort_dbg[14], 0u, 1u) == 0u) {
+                g_sort_dbg[15] = (uint32_t)((tile & 0xffffu) << 16 | (warp << 12) | (sum & 0xfffu));
+            }
+        }
+        __syncthreads();
+#endif
+        // per-digit tile totals; warp counts become warp-exclusive prefixes
+        uint32_t run = 0;
+#pragma unroll
+        for (int w = 0; w < kWarps; ++w) {
+            const uint32_t c = s_whist[w * kBins + tid];
+            s_whist[w * kBins + tid] = run;
+            run += c;
+        }
+        s_total[tid] = run;
+        {
+            unsigned long long* lb = a.lookback + (size_t)tile * kBins + tid;
+            const unsigned long long ep = (unsigned long long)a.epoch << 32;
+            st_volatile_u64(lb, (tile == 0 ? kFlagInc : kFlagAgg) | ep | run);
+            uint32_t excl = 0;
+            if (tile > 0) {
+                int64_t j = tile - 1;
+                uint32_t spins = 0;
+                while (j >= 0) {
+                    const unsigned long long w = ld_volatile_u64(a.lookback + (size_t)j * kBins + tid);
+                    const uint32_t wep = (uint32_t)(w >> 32) & 0x3fffffffu;
+                    const unsigned long long flag = w & (3ull << 62);
+                    if (wep != a.epoch || flag == 0) {
+                        if (++spins > kSpinLimit) {
+                            record_error(a.status, MSC_ERR_INTERNAL);
+                            break;
+                        }
+                        __nanosleep(32);
+                        continue;
+                    }
+                    excl += (uint32_t)w;
+                    if (flag == kFlagInc) break;
+                    --j;
+                }
+                st_volatile_u64(lb, kFlagInc | ep | (unsigned long long)(excl + run));
+            }
+            s_gbase[tid] = s_bstart[tid] + excl;
+        }
+        s_excl[tid] = block_scan_256(run, s_misc + 1) - run;
+        __syncthreads();  // s_excl is read across threads below
+        if constexpr (TO_ORDER) {
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                const uint32_t d = rk[k] >> 16;
+                if (d < 256u) {
+                    const uint32_t pos = s_gbase[d] + s_whist[warp * kBins + d] + (rk[k] & 0xffffu);
+                    MSC_GUARD((uint32_t)val[k] < (uint64_t)n && pos < (uint64_t)n, a.status, -101)
+                    a.order_out[val[k]] = (int32_t)pos;
+                }
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < kItems; ++k) {
+                const uint32_t d = rk[k] >> 16;
+                if (d < 256u) {
+                    const uint32_t lpos = s_excl[d] + s_whist[warp * kBins + d] + (rk[k] & 0xffffu);
+#ifdef MSC_DEBUG_BOUNDS
+                    if (lpos >= (uint32_t)kSortTile && atomicCAS(&g_sort_dbg[0], 0u, 1u) == 0u) {
+                        g_sort_dbg[1] = (uint32_t)tile; g_sort_dbg[2] = warp; g_sort_dbg[3] = lane;
+                        g_sort_dbg[4] = k; g_sort_dbg[5] = d; g_sort_dbg[6] = s_excl[d];
+                        g_sort_dbg[7] = s_whist[warp * kBins + d]; g_sort_dbg[8] = rk[k] & 0xffffu;
+                        g_sort_dbg[9] = a.shift; g_sort_dbg[10] = s_total[d]; g_sort_dbg[11] = blockIdx.x;
+                        g_sort_dbg[12] = (uint32_t)ntiles; g_sort_dbg[13] = gridDim.x;
+                    }
+#endif
+                    MSC_GUARD(lpos < (uint32_t)kSortTile, a.status, -103) {
+                        s_keys[lpos] = key[k];
+                        s_vals[lpos] = val[k];
+                    }
+                }
+            }
+            __syncthreads();
+            const int cnt = (int)min((int64_t)kSortTile, n - tile * kSortTile);
+            for (int i = tid; i < cnt; i += kThreads) {
+                const KeyT kk = s_keys[i];
+                const uint32_t d = (uint32_t)(kk >> a.shift) & 255u;
+                const uint32_t pos = s_gbase[d] + (uint32_t)i - s_excl[d];
+                MSC_GUARD(pos < (uint64_t)n, a.status, -102) {
+                    a.keys_out[pos] = kk;
+                    a.vals_out[pos] = s_vals[i];
+                }
+            }
+        }
+        __syncthreads();
+    }
+}
+
+template <typename KeyT, bool FROM_F, bool TO_ORDER>
+int launch_pass(const PassArgs<KeyT>& a, int64_t max_n, cudaStream_t s) {
+    constexpr size_t smem = pass_smem_bytes<KeyT, !TO_ORDER>();
+    auto kern = k_onesweep<KeyT, FROM_F, TO_ORDER>;
+    static int configured_dev = -1;  // the attribute is set once per device
+    if (configured_dev != current_device().id) {
+        MSC_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        configured_dev = current_device().id;
+    }
+    int occ = 0;
+    MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
+    const int64_t ntiles = ceil_div(max_n, kSortTile);
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)current_device().sms * std::max(occ, 1)));
+    kern<<<(unsigned)grid, kThreads, smem, s>>>(a);
+    MSC_LAUNCHED();
+    return MSC_OK;
+}
+
+}  // namespace
+
+void size_sort_scratch(Sizer& s, int64_t n) {
+    s.take<uint32_t>(8 * kBins + 8);
+    s.take<unsigned long long>((size_t)std::max<int64_t>(1, ceil_div(n, kSortTile)) * kBins);
+}
+
+SortScratch carve_sort_scratch(Carver& c, int64_t n) {
+    SortScratch sc;
+    sc.hist = c.take<uint32_t>(8 * kBins + 8);
+    sc.tile_counters = sc.hist + 8 * kBins;
+    sc.max_tiles = std::max<int64_t>(1, ceil_div(n, kSortTile));
+    sc.lookback = c.take<unsigned long long>((size_t)sc.max_tiles * kBins);
+    return sc;
+}
+
+static int clear_scratch(const SortScratch& sc, int64_t n, cudaStream_t s) {
+    MSC_TRY(cudaMemsetAsync(sc.hist, 0, (8 * kBins + 8) * sizeof(uint32_t), s));
+    const int64_t tiles = std::max<int64_t>(1, ceil_div(n, kSortTile));
+    MSC_TRY(cudaMemsetAsync(sc.lookback, 0, (size_t)tiles * kBins * sizeof(unsigned long long), s));
+    return MSC_OK;
+}
+
+static int hist_grid(int64_t n) {
+    const int64_t want = ceil_div(std::max<int64_t>(n, 1), 256 * 8);
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)current_device().sms * 8));
+}
+
+int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_t* id_a,
+              uint32_t* key_b, int32_t* id_b, const SortScratch& sc, int32_t* status,
+              cudaStream_t s) {
+    if (n <= 0) return MSC_OK;
+    int r = clear_scratch(sc, n, s);
+    if (r) return r;
+    k_hist<uint32_t, true><<<hist_grid(n), 256, 0, s>>>(nullptr, f, n, nullptr, 4, sc.hist, status);
+    MSC_LAUNCHED();
+    PassArgs<uint32_t> a{};
+    a.n = n;
+    a.status = status;
+    a.lookback = sc.lookback;
+    // pass 0: float field -> (key_a, id_a)
+    a.f_in = f;
+    a.keys_out = key_a;
+    a.vals_out = id_a;
+    a.hist = sc.hist;
+    a.shift = 0;
+    a.tile_counter = sc.tile_counters + 0;
+    a.epoch = 1;
+    if ((r = launch_pass<uint32_t, true, false>(a, n, s))) return r;
+    // pass 1: a -> b ; pass 2: b -> a
+    uint32_t* kin = key_a;
+    int32_t* iin = id_a;
+    uint32_t* kout = key_b;
+    int32_t* iout = id_b;
+    for (int p = 1; p <= 2; ++p) {
+        a.f_in = nullptr;
+        a.keys_in = kin;
+        a.vals_in = iin;
+        a.keys_out = kout;
+        a.vals_out = iout;
+        a.hist = sc.hist + p * kBins;
+        a.shift = 8 * p;
+        a.tile_counter = sc.tile_counters + p;
+        a.epoch = (uint32_t)(p + 1);
+        if ((r = launch_pass<uint32_t, false, false>(a, n, s))) return r;
+        std::swap(kin, kout);
+        std::swap(iin, iout);
+    }
+    // pass 3: a -> order
+    a.keys_in = kin;
+    a.vals_in = iin;
+    a.keys_out = nullptr;
+    a.vals_out = nullptr;
+    a.order_out = order;
+    a.hist = sc.hist + 3 * kBins;
+    a.shift = 24;
+    a.tile_counter = sc.tile_counters + 3;
+    a.epoch = 4;
+    return launch_pass<uint32_t, false, true>(a, n, s);
+}
+
+int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* keys_alt,
+                 int32_t* vals_alt, const int32_t* d_count, int64_t max_count, int key_bits,
+                 const SortScratch& sc, int32_t* status, cudaStream_t s, bool* result_in_alt) {
+    *result_in_alt = false;
+    if (max_count <= 0 || key_bits <= 0) return MSC_OK;
+    const int npass = std::min(8, (key_bits + 7) / 8);
+    int r = clear_scratch(sc, max_count, s);
+    if (r) return r;
+    k_hist<unsigned long long, false><<<hist_grid(max_count), 256, 0, s>>>(keys, nullptr, max_count, d_count, npass, sc.hist, status);
+    MSC_LAUNCHED();
+    PassArgs<unsigned long long> a{};
+    a.n = max_count;
+    a.d_n = d_count;
+    a.status = status;
+    a.lookback = sc.lookback;
+    unsigned long long* kin = keys;
+    int32_t* vin = vals;
+    unsigned long long* kout = keys_alt;
+    int32_t* vout = vals_alt;
+    for (int p = 0; p < npass; ++p) {
+        a.keys_in = kin;
+        a.vals_in = vin;
+        a.keys_out = kout;
+        a.vals_out = vout;
+        a.hist = sc.hist + p * kBins;
+        a.shift = 8 * p;
+        a.tile_counter = sc.tile_counters + p;
+        a.epoch = (uint32_t)(p + 1);
+        if ((r = launch_pass<unsigned long long, false, false>(a, max_count, s))) return r;
+        std::swap(kin, kout);
+        std::swap(vin, vout);
+    }
+    *result_in_alt = (npass & 1) != 0;
+    return MSC_OK;
+}
+
+}  // namespace msc
+
+#ifdef MSC_DEBUG_BOUNDS
+extern "C" MSC_API int msc_debug_sort(uint32_t* out16) {
+    return cudaMemcpyFromSymbol(out16, msc::g_sort_dbg, sizeof(uint32_t) * 16) == cudaSuccess ? 0 : -3;
+}
+#endif

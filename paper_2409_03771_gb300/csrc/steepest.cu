@@ -1,0 +1,374 @@
+// Steepest-ascent / steepest-descent pointers on the implicit Freudenthal
+// triangulation of a regular grid (Alg. 1 initialisation, and its mirror
+// for the ascending manifold), plus the explicit-adjacency (CSR) variant.
+//
+// Grid kernel: persistent CTAs walk 32x8x8 vertex tiles.  Each tile's
+// order values plus a halo (4 cells in x to keep the TMA x coordinate
+// 16-byte aligned, 1 cell in y and z) land in shared memory through one 3D
+// TMA box (40x10x10 int32), double-buffered against the compute of the
+// previous tile.  Cells outside the grid get -1, which loses every signed
+// max and (as 0xffffffff) every unsigned min, so border vertices see only
+// their in-grid neighbours.  A thread handles four consecutive x vertices
+// in two z planes, reading each neighbour row once as an int4 plus edge
+// scalars, and keeps argmax / argmin as packed (order * 16 + code) keys.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <type_traits>
+
+#include "common.cuh"
+#include "steepest.cuh"
+#include "tma.cuh"
+
+namespace msc {
+namespace {
+
+constexpr int TX = 32, TY = 8, TZ = 8;
+constexpr int BX = TX + 8, BY = TY + 2, BZ = TZ + 2;
+constexpr int PLANE = BX * BY;  // 400
+constexpr int BOX = PLANE * BZ;  // 4000
+constexpr int kThreads = 256;
+constexpr uint32_t kWaitLimit = 1u << 22;
+
+// Neighbour codes 0..13 (matching the row reads below), 14 = the vertex.
+__constant__ int8_t c_off[15][3] = {
+    {0, 0, -1}, {-1, 0, -1}, {0, -1, -1}, {-1, -1, -1}, {0, -1, 0},
+    {-1, -1, 0}, {-1, 0, 0}, {1, 0, 0},   {0, 1, 0},    {1, 1, 0},
+    {0, 0, 1},  {1, 0, 1},  {0, 1, 1},    {1, 1, 1},    {0, 0, 0}};
+
+struct GridInfo {
+    int32_t nx, ny, nz;
+    int32_t tx, ty;  // tiles along x and y
+    int64_t ntiles;
+    int vec_store;  // asc/desc rows can take int4 stores
+};
+
+template <typename PK>
+struct Best {
+    PK hi, lo;  // hi: signed max, lo: unsigned min
+    __device__ __forceinline__ void init(int c) { hi = lo = (PK)c * 16 + 14; }
+    __device__ __forceinline__ void add(int val, int code) {
+        const PK p = (PK)val * 16 + code;
+        hi = p > hi ? p : hi;
+        using U = typename std::conditional<sizeof(PK) == 4, uint32_t, unsigned long long>::type;
+        lo = (U)p < (U)lo ? p : lo;
+    }
+};
+
+__device__ __forceinline__ void load_row(const int* r, int (&o)[6]) {
+    // o[j] = value at x offset j-1 relative to the thread's first vertex
+    const int4 q = *reinterpret_cast<const int4*>(r);
+    o[0] = r[-1];
+    o[1] = q.x;
+    o[2] = q.y;
+    o[3] = q.z;
+    o[4] = q.w;
+    o[5] = r[4];
+}
+
+template <typename PK>
+__device__ __forceinline__ void tile_compute(const int* buf, const GridInfo& g, int x0, int y0,
+                                             int z0, const int64_t* s_off, int32_t* __restrict__ asc,
+                                             int32_t* __restrict__ desc, uint32_t& nmin,
+                                             uint32_t& nmax) {
+    const int tid = threadIdx.x;
+    const int xq = tid & 7, ly = (tid >> 3) & 7, lzq = tid >> 6;
+    const int gx0 = x0 + 4 * xq, gy = y0 + ly;
+    if (gx0 >= g.nx || gy >= g.ny) return;
+#pragma unroll
+    for (int rep = 0; rep < 2; ++rep) {
+        const int lz = lzq + 4 * rep;
+        const int gz = z0 + lz;
+        if (gz >= g.nz) break;
+        const int* b = buf + (lz + 1) * PLANE + (ly + 1) * BX + 4 * xq + 4;
+        int A[6], B[6], C[6], D[6], E[6], F[6], G[6];
+        load_row(b - PLANE, A);
+        load_row(b - PLANE - BX, B);
+        load_row(b - BX, C);
+        load_row(b, D);
+        load_row(b + BX, E);
+        load_row(b + PLANE, F);
+        load_row(b + PLANE + BX, G);
+        int hi_code[4], lo_code[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            const int j = i + 1;  // index of x offset 0
+            Best<PK> bst;
+            bst.init(D[j]);
+            bst.add(A[j], 0);
+            bst.add(A[j - 1], 1);
+            bst.add(B[j], 2);
+            bst.add(B[j - 1], 3);
+            bst.add(C[j], 4);
+            bst.add(C[j - 1], 5);
+            bst.add(D[j - 1], 6);
+            bst.add(D[j + 1], 7);
+            bst.add(E[j], 8);
+            bst.add(E[j + 1], 9);
+            bst.add(F[j], 10);
+            bst.add(F[j + 1], 11);
+            bst.add(G[j], 12);
+            bst.add(G[j + 1], 13);
+            hi_code[i] = (int)(bst.hi & 15);
+            lo_code[i] = (int)(bst.lo & 15);
+        }
+        const int64_t v0 = gx0 + (int64_t)g.nx * (gy + (int64_t)g.ny * gz);
+        int out_hi[4], out_lo[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            out_hi[i] = (int)(v0 + i + s_off[hi_code[i]]);
+            out_lo[i] = (int)(v0 + i + s_off[lo_code[i]]);
+            nmax += hi_code[i] == 14 && gx0 + i < g.nx;
+            nmin += lo_code[i] == 14 && gx0 + i < g.nx;
+        }
+#ifdef MSC_DEBUG_BOUNDS
+        if (v0 < 0 || v0 + 3 >= (int64_t)g.nx * g.ny * g.nz + 3) return;
+#endif
+        if (g.vec_store && gx0 + 3 < g.nx) {
+            *reinterpret_cast<int4*>(desc + v0) = make_int4(out_hi[0], out_hi[1], out_hi[2], out_hi[3]);
+            *reinterpret_cast<int4*>(asc + v0) = make_int4(out_lo[0], out_lo[1], out_lo[2], out_lo[3]);
+        } else {
+#pragma unroll
+            for (int i = 0; i < 4; ++i)
+                if (gx0 + i < g.nx) {
+                    desc[v0 + i] = out_hi[i];
+                    asc[v0 + i] = out_lo[i];
+                }
+        }
+    }
+}
+
+__device__ __forceinline__ void tile_coords(const GridInfo& g, int64_t tile, int& x0, int& y0,
+                                            int& z0) {
+    const int64_t txy = (int64_t)g.tx * g.ty;
+    const int64_t tz = tile / txy;
+    const int64_t r = tile - tz * txy;
+    const int64_t ty = r / g.tx;
+    x0 = (int)((r - ty * g.tx) * TX);
+    y0 = (int)(ty * TY);
+    z0 = (int)(tz * TZ);
+}
+
+__device__ __forceinline__ bool box_crosses_border(const GridInfo& g, int x0, int y0, int z0) {
+    return x0 < 4 || y0 < 1 || z0 < 1 || x0 + TX + 4 > g.nx || y0 + TY + 1 > g.ny ||
+           z0 + TZ + 1 > g.nz;
+}
+
+__device__ __forceinline__ void mark_outside(int* buf, const GridInfo& g, int x0, int y0, int z0) {
+    for (int i = threadIdx.x; i < BOX; i += kThreads) {
+        const int lz = i / PLANE, r = i - lz * PLANE, ly = r / BX, lx = r - ly * BX;
+        const int gx = x0 - 4 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
+        if (gx < 0 || gy < 0 || gz < 0 || gx >= g.nx || gy >= g.ny || gz >= g.nz) buf[i] = -1;
+    }
+}
+
+__device__ __forceinline__ void flush_counts(uint32_t nmin, uint32_t nmax, uint32_t* extrema) {
+    if (!extrema) return;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+        nmin += __shfl_xor_sync(0xffffffffu, nmin, o);
+        nmax += __shfl_xor_sync(0xffffffffu, nmax, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        if (nmin) atomicAdd(&extrema[0], nmin);
+        if (nmax) atomicAdd(&extrema[1], nmax);
+    }
+}
+
+template <typename PK>
+__global__ void __launch_bounds__(kThreads) k_steepest_tma(const __grid_constant__ CUtensorMap map,
+                                                          const GridInfo g, int32_t* asc,
+                                                          int32_t* desc, uint32_t* extrema,
+                                                          int32_t* status) {
+    __shared__ alignas(128) int buf[2][BOX];
+    __shared__ alignas(8) uint64_t bar[2];
+    __shared__ int64_t s_off[15];
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        mbar_init(&bar[0], 1);
+        mbar_init(&bar[1], 1);
+        fence_mbar_init();
+    }
+    if (tid < 15)
+        s_off[tid] = c_off[tid][0] + (int64_t)g.nx * (c_off[tid][1] + (int64_t)g.ny * c_off[tid][2]);
+    __syncthreads();
+    auto issue = [&](int64_t t, int b) {
+        int x0, y0, z0;
+        tile_coords(g, t, x0, y0, z0);
+        mbar_expect_tx(&bar[b], BOX * 4);
+        tma_load_3d(buf[b], &map, x0 - 4, y0 - 1, z0 - 1, &bar[b]);
+    };
+    int64_t tile = blockIdx.x;
+    if (tid == 0) {
+        if (tile < g.ntiles) issue(tile, 0);
+        if (tile + gridDim.x < g.ntiles) issue(tile + gridDim.x, 1);
+    }
+    uint32_t phase[2] = {0u, 0u};
+    uint32_t nmin = 0, nmax = 0;
+    for (int it = 0; tile < g.ntiles; ++it, tile += gridDim.x) {
+        const int b = it & 1;
+        const bool ok = mbar_wait(&bar[b], phase[b], kWaitLimit);
+        if (__syncthreads_or(!ok)) {  // never expected: give up cleanly
+            if (tid == 0) record_error(status, MSC_ERR_INTERNAL);
+            mbar_wait(&bar[b], phase[b], kWaitLimit);
+            mbar_wait(&bar[b ^ 1], phase[b ^ 1], kWaitLimit);
+            return;
+        }
+        phase[b] ^= 1u;
+        int x0, y0, z0;
+        tile_coords(g, tile, x0, y0, z0);
+        if (box_crosses_border(g, x0, y0, z0)) {
+            mark_outside(buf[b], g, x0, y0, z0);
+            __syncthreads();
+        }
+        tile_compute<PK>(buf[b], g, x0, y0, z0, s_off, asc, desc, nmin, nmax);
+        __syncthreads();
+        if (tid == 0 && tile + 2 * (int64_t)gridDim.x < g.ntiles) {
+            fence_proxy_async_smem();
+            issue(tile + 2 * (int64_t)gridDim.x, b);
+        }
+    }
+    flush_counts(nmin, nmax, extrema);
+}
+
+// Same stencil with plain coalesced loads (grids whose rows TMA cannot
+// address: nx not a multiple of 4, or an unaligned base pointer).
+template <typename PK>
+__global__ void __launch_bounds__(kThreads) k_steepest_ld(const int32_t* __restrict__ order,
+                                                         const GridInfo g, int32_t* asc,
+                                                         int32_t* desc, uint32_t* extrema) {
+    __shared__ alignas(16) int buf[BOX];
+    __shared__ int64_t s_off[15];
+    const int tid = threadIdx.x;
+    if (tid < 15)
+        s_off[tid] = c_off[tid][0] + (int64_t)g.nx * (c_off[tid][1] + (int64_t)g.ny * c_off[tid][2]);
+    uint32_t nmin = 0, nmax = 0;
+    for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
+        int x0, y0, z0;
+        tile_coords(g, tile, x0, y0, z0);
+        for (int i = tid; i < BOX; i += kThreads) {
+            const int lz = i / PLANE, r = i - lz * PLANE, ly = r / BX, lx = r - ly * BX;
+            const int gx = x0 - 4 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
+            int val = -1;
+            if (gx >= 0 && gy >= 0 && gz >= 0 && gx < g.nx && gy < g.ny && gz < g.nz)
+                val = order[gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz)];
+            buf[i] = val;
+        }
+        __syncthreads();
+        tile_compute<PK>(buf, g, x0, y0, z0, s_off, asc, desc, nmin, nmax);
+        __syncthreads();
+    }
+    flush_counts(nmin, nmax, extrema);
+}
+
+// ----------------------------------------------------------------------------
+// CSR variant: 8 lanes per vertex, each lane scans every 8th neighbour.
+
+constexpr int kCsrLanes = 8;
+
+__global__ void __launch_bounds__(256) k_steepest_csr(const int32_t* __restrict__ order,
+                                                      const int32_t* __restrict__ row,
+                                                      const int32_t* __restrict__ col, int32_t n,
+                                                      int32_t* asc, int32_t* desc,
+                                                      int32_t* status) {
+    const int sub = threadIdx.x & (kCsrLanes - 1);
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    constexpr int kPerWarp = 32 / kCsrLanes;
+    // warp-uniform loop: the warp's 4 vertices are wbase .. wbase+3
+    for (int64_t wbase = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32) * kPerWarp;
+         wbase < n; wbase += warps * kPerWarp) {
+        const int64_t v = wbase + (threadIdx.x & 31) / kCsrLanes;
+        const bool live = v < n;
+        int hi_v = -1, hi_u = -1, lo_v = INT32_MAX, lo_u = -1;
+        if (live) {
+            const int ov = order[v];
+            hi_v = ov;
+            hi_u = (int)v;
+            lo_v = ov;
+            lo_u = (int)v;
+            const int e0 = row[v], e1 = row[v + 1];
+            for (int e = e0 + sub; e < e1; e += kCsrLanes) {
+                const int u = col[e];
+                if ((unsigned)u >= (unsigned)n) {
+                    record_error(status, MSC_ERR_ARG);
+                    continue;
+                }
+                const int ou = order[u];
+                if (ou > hi_v) {
+                    hi_v = ou;
+                    hi_u = u;
+                }
+                if (ou < lo_v) {
+                    lo_v = ou;
+                    lo_u = u;
+                }
+            }
+        }
+#pragma unroll
+        for (int o = kCsrLanes / 2; o > 0; o >>= 1) {
+            const int hv = __shfl_xor_sync(0xffffffffu, hi_v, o);
+            const int hu = __shfl_xor_sync(0xffffffffu, hi_u, o);
+            const int lv = __shfl_xor_sync(0xffffffffu, lo_v, o);
+            const int lu = __shfl_xor_sync(0xffffffffu, lo_u, o);
+            if (hv > hi_v) {
+                hi_v = hv;
+                hi_u = hu;
+            }
+            if (lv < lo_v) {
+                lo_v = lv;
+                lo_u = lu;
+            }
+        }
+        if (live && sub == 0) {
+            desc[v] = hi_u;
+            asc[v] = lo_u;
+        }
+    }
+}
+
+}  // namespace
+
+int run_steepest_grid(const int32_t* order, msc_grid gd, int32_t* asc, int32_t* desc,
+                      uint32_t* extrema, int32_t* status, cudaStream_t s, bool allow_tma) {
+    GridInfo g;
+    g.nx = gd.nx;
+    g.ny = gd.ny;
+    g.nz = gd.nz;
+    g.tx = (int)ceil_div(gd.nx, TX);
+    g.ty = (int)ceil_div(gd.ny, TY);
+    const int64_t tz = ceil_div(gd.nz, TZ);
+    g.ntiles = (int64_t)g.tx * g.ty * tz;
+    g.vec_store = (gd.nx % 4 == 0) && ((uintptr_t)asc % 16 == 0) && ((uintptr_t)desc % 16 == 0);
+    const int64_t n = (int64_t)gd.nx * gd.ny * gd.nz;
+    const bool packed = n <= (int64_t(1) << 27);
+    const int sms = current_device().sms;
+    CUtensorMap map;
+    const bool tma = allow_tma && make_tensor_map_3d(&map, order, 4, gd.nx, gd.ny, gd.nz, BX, BY, BZ);
+    int occ = 1;
+    if (tma) {
+        auto kern = packed ? k_steepest_tma<int32_t> : k_steepest_tma<int64_t>;
+        MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)sms * std::max(occ, 1)));
+        kern<<<(unsigned)grid, kThreads, 0, s>>>(map, g, asc, desc, extrema, status);
+    } else {
+        auto kern = packed ? k_steepest_ld<int32_t> : k_steepest_ld<int64_t>;
+        MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
+        const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)sms * std::max(occ, 1)));
+        kern<<<(unsigned)grid, kThreads, 0, s>>>(order, g, asc, desc, extrema);
+    }
+    MSC_LAUNCHED();
+    return MSC_OK;
+}
+
+int run_steepest_csr(const int32_t* order, const int32_t* row, const int32_t* col, int32_t n,
+                     int32_t* asc, int32_t* desc, int32_t* status, cudaStream_t s) {
+    if (n <= 0) return MSC_OK;
+    const int64_t want = ceil_div((int64_t)n * kCsrLanes, 256);
+    const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)current_device().sms * 8));
+    k_steepest_csr<<<grid, 256, 0, s>>>(order, row, col, n, asc, desc, status);
+    MSC_LAUNCHED();
+    return MSC_OK;
+}
+
+}  // namespace msc
