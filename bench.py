@@ -1,0 +1,439 @@
+#!/usr/bin/env python3
+"""Throughput of the Morse-Smale segmentation + connected-components hot path
+on one GB300 (replicas on N GPUs), in vertices per second.
+
+One step = the whole hot path over one batch of synthetic input:
+  * msc_segment on a 512^3 sum of 64 Gaussians (order, steepest pointers,
+    path compression of both, Morse-Smale ids),
+  * msc_segment on a 512^3 white-noise field (heavy ties, ~46M cells),
+  * msc_cc_mask on a 512^3 feature mask (6-connectivity),
+  * msc_cc_mesh on a thinned, permuted 256^3 Kuhn tetrahedral mesh.
+value = vertices processed per second (all four calls) over all ranks.
+
+--impl reference times the plain CPU oracle (the only other implementation
+of the method: the paper's code is CPU C++ inside TTK and not available) on
+a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "vertices/s and % HBM roofline for MS segmentation + CC at 512^3; batched/served p50/p99"
+EDGE = 512
+MESH_EDGE = 256
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--edge", type=int, default=EDGE, help="grid edge (512 is the benchmarked size)")
+    ap.add_argument("--mesh-edge", type=int, default=MESH_EDGE)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# helpers
+
+
+def dist_info():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            p = json.load(fh)
+        return float(p["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "100",
+                 "-i", str(self.gpu)], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                out, _ = self.proc.communicate(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+                out, _ = self.proc.communicate()
+            self.out = out
+        return False
+
+    def summary(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in getattr(self, "out", "").strip().splitlines():
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for nm, val in zip(names, parts[5:9]):
+                if val.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def kernel_sources_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2409_03771_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, f), "rb") as fh:
+            h.update(f.encode() + fh.read())
+    return h.hexdigest()[:16]
+
+
+def committed_traffic(label):
+    """DRAM bytes per vertex of a kernel from a committed ncu summary, if the
+    kernel sources have not changed since it was taken."""
+    path = os.path.join(ROOT, "profiles", "traffic.json")
+    if not os.path.exists(path):
+        return None
+    with open(path) as fh:
+        t = json.load(fh)
+    if t.get("sources_sha") != kernel_sources_sha():
+        return None
+    e = t.get("kernels", {}).get(label)
+    return None if e is None else float(e["dram_bytes_per_vertex"])
+
+
+# Algorithmic bytes per launch of each traced kernel, as functions of the
+# step's sizes (n = grid vertices, nm / nnz = mesh vertices / CSR entries).
+def algorithmic_bytes(label, n, nm, nnz):
+    table = {
+        "order.hist": 4 * n,             # read f
+        "order.pass_first": 12 * n,      # read f, write (key, id)
+        "order.pass": 16 * n,            # read and write (key, id)
+        "order.pass_last": 12 * n,       # read (key, id), write order
+        "steepest.grid": 12 * n,         # read order, write asc + desc
+        "msid.insert": 12 * n,           # read asc + desc, write slot
+        "msid.lookup": 8 * n,            # read slot, write id
+        "cc.local": 5 * n,               # read mask, write label
+        "cc.flatten": 8 * n,             # read label, write label
+        "mesh.init": 8 * nm + 4 * nnz,   # read row + col, write label
+        "mesh.hook": 4 * nm + 4 * nnz,   # read row + col
+        "mesh.flatten": 8 * nm,
+    }
+    return table.get(label)
+
+
+# ---------------------------------------------------------------------------
+# our implementation
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_2409_03771_gb300 as msc
+    import workloads
+
+    rank, world, local = dist_info()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=dev)
+    msc.load()
+
+    E, ME = args.edge, args.mesh_edge
+    dims = (E, E, E)
+    n = E ** 3
+    t0 = time.time()
+    f_smooth = workloads.field_smooth(edge=E, seed=1, device=dev).reshape(-1)
+    f_noise = workloads.field_noise(edge=E, seed=1, device=dev).reshape(-1)
+    mask = workloads.mask_blobs(edge=E, seed=2, device=dev).reshape(-1)
+    row, col = workloads.tet_mesh_csr(edge=ME, delete_frac=0.4, seed=3, device=dev)
+    nm, nnz = row.numel() - 1, col.numel()
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+
+    i32 = dict(dtype=torch.int32, device=dev)
+    seg_out = [[torch.empty(n, **i32) for _ in range(4)] for _ in range(2)]
+    cells = torch.zeros(2, **i32)
+    lab = torch.empty(n, **i32)
+    mlab = torch.empty(nm, **i32)
+    ws = torch.empty(msc.msc_workspace_bytes(msc.OP_SEGMENT, n), dtype=torch.uint8, device=dev)
+    small_ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    status = torch.zeros(4, **i32)
+    stream = torch.cuda.current_stream(dev)
+
+    def step(fs, fn, mk, rw, cl):
+        for j, f in enumerate((fs, fn)):
+            o = seg_out[j]
+            r = msc.msc_segment(f, dims, o[0], o[1], o[2], o[3], cells[j:j + 1], ws, ws.numel(),
+                                status[j:j + 1], stream)
+            assert r == 0, msc.msc_status_string(r)
+        r = msc.msc_cc_mask(mk, dims, 6, lab, small_ws, small_ws.numel(), status[2:3], stream)
+        assert r == 0, msc.msc_status_string(r)
+        r = msc.msc_cc_mesh(rw, cl, nm, mlab, small_ws, small_ws.numel(), status[3:4], stream)
+        assert r == 0, msc.msc_status_string(r)
+
+    def check_status(where):
+        s = status.cpu().tolist()
+        if any(s):
+            raise RuntimeError(f"{where}: device status {s}")
+
+    verts = 3 * n + nm
+    for _ in range(args.warmup):
+        step(f_smooth, f_noise, mask, row, col)
+    torch.cuda.synchronize()
+    check_status("warm-up")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    # ---- timed region (device) ----
+    msc.msc_trace_reset()
+    msc.msc_trace_enable(True)
+    launches0 = msc.msc_launch_count()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    barrier()
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        time.sleep(0.25)  # let the sampler start before the timed region
+        ev0.record(stream)
+        for _ in range(args.steps):
+            step(f_smooth, f_noise, mask, row, col)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    barrier()
+    launches = msc.msc_launch_count() - launches0
+    msc.msc_trace_enable(False)
+    trace = msc.msc_trace_collect()
+    check_status("timed region")
+    ms = ev0.elapsed_time(ev1) / args.steps
+    t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    value = world * verts / (ms_max / 1e3)
+
+    # ---- end to end: pinned host inputs in, results back to host ----
+    e2e = None
+    if not args.no_e2e:
+        h_in = [x.cpu().pin_memory() for x in (f_smooth, f_noise, mask, row, col)]
+        d_in = [torch.empty_like(x) for x in (f_smooth, f_noise, mask, row, col)]
+        outs = seg_out[0] + seg_out[1] + [cells, lab, mlab]
+        h_out = [torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in outs]
+        h2d = sum(x.numel() * x.element_size() for x in h_in)
+        d2h = sum(x.numel() * x.element_size() for x in h_out)
+
+        def e2e_step():
+            for d, h in zip(d_in, h_in):
+                d.copy_(h, non_blocking=True)
+            step(*d_in)
+            for h, d in zip(h_out, outs):
+                h.copy_(d, non_blocking=True)
+
+        e2e_step()
+        torch.cuda.synchronize()
+        ee = max(1, min(args.steps, 5))
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(ee):
+            e2e_step()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+        check_status("e2e")
+        e_ms = ev0.elapsed_time(ev1) / ee
+        t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
+        if world > 1:
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e = {"value": world * verts / (float(t.item()) / 1e3), "unit": "vertices/s",
+               "ms_per_step": float(t.item()), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+
+    # ---- roofline of the dominant kernel (live trace over the timed region) ----
+    peak, peak_kind = measured_peaks()
+    stages = {k: round(v[1] / args.steps, 4) for k, v in sorted(trace.items(), key=lambda kv: -kv[1][1])}
+    roofline = None
+    for label, (cnt, tot) in sorted(trace.items(), key=lambda kv: -kv[1][1]):
+        b = algorithmic_bytes(label, n, nm, nnz)
+        if b is None:
+            continue
+        avg_s = tot / cnt / 1e3
+        achieved = b / avg_s / 1e9
+        tb = committed_traffic(label)
+        roofline = {"bound": "hbm", "kernel": label, "achieved": round(achieved, 1), "peak": peak,
+                    "unit": "GB/s", "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                    "traffic": None if tb is None else tb * (nm if label.startswith("mesh") else n),
+                    "algorithmic_bytes": b, "avg_launch_ms": round(tot / cnt, 4),
+                    "share_of_step": round(tot / args.steps / ms, 4)}
+        break
+
+    out = {
+        "metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_max, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {
+            "workload": (f"segment {E}^3 Gaussian sum (64, seed 1) + segment {E}^3 white noise (seed 1) + "
+                         f"6-conn CC of a {E}^3 mask (256 Gaussians > 0.3, seed 2) + CC of a {ME}^3 Kuhn "
+                         f"mesh (40% tets deleted, permuted, seed 3)"),
+            "vertices_per_step": verts, "mesh_vertices": nm, "mesh_nnz": nnz,
+            "cells": [int(c) for c in cells.cpu().tolist()],
+            "mask_fraction": round(float(mask.float().mean().item()), 4),
+            "l2": "inputs larger than L2 (512 MiB fields, 128 MiB mask, 0.9 GiB CSR); no flush",
+            "parallelism": f"replicas x{world}", "input_gen_s": round(gen_s, 1),
+        },
+        "clocks": clk.summary(),
+        "e2e": e2e,
+        "gpu_launches": int(launches),
+        "roofline": roofline,
+        "stages_ms_per_step": stages,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(f_smooth, f_noise, mask, E)
+    if rank == 0:
+        print(json.dumps(out), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm)
+
+
+SAMPLE_MESH_EDGE = 96
+
+
+def oracle_sample(f_smooth, f_noise, mask, E):
+    """Host copies of a bounded sample of the step's workload (a few seconds
+    of single-core oracle work): 8 z-planes of each field (a 512x512x8 grid),
+    16 z-planes of the mask, and a 96^3 mesh made with the same recipe."""
+    import workloads
+
+    zs, zm = 8, 16
+    fs = f_smooth.reshape(E, E, E)[:zs].contiguous().cpu().numpy().ravel()
+    fn = f_noise.reshape(E, E, E)[:zs].contiguous().cpu().numpy().ravel()
+    mk = mask.reshape(E, E, E)[:zm].contiguous().cpu().numpy().ravel()
+    row, col = workloads.tet_mesh_csr(edge=SAMPLE_MESH_EDGE, delete_frac=0.4, seed=3, device=f_smooth.device)
+    return {"fs": (fs, (E, E, zs)), "fn": (fn, (E, E, zs)), "mk": (mk, (E, E, zm)),
+            "mesh": (row.cpu().numpy(), col.cpu().numpy()),
+            "desc": f"segment of {E}x{E}x{zs} slabs of both fields, 6-conn CC of a {E}x{E}x{zm} mask slab, "
+                    f"CC of a {SAMPLE_MESH_EDGE}^3 mesh of the same recipe ({row.numel() - 1} vertices)"}
+
+
+def oracle_step(sample):
+    import oracle
+
+    verts = 0
+    for key in ("fs", "fn"):
+        f, d = sample[key]
+        oracle.segment_grid(f, d)
+        verts += f.size
+    m, d = sample["mk"]
+    oracle.cc_grid(m, d, 6)
+    verts += m.size
+    row, col = sample["mesh"]
+    oracle.cc_csr(row, col)
+    verts += row.size - 1
+    return verts
+
+
+def cpu_baseline(f_smooth, f_noise, mask, E):
+    import oracle
+
+    oracle.build()
+    sample = oracle_sample(f_smooth, f_noise, mask, E)
+    t0 = time.perf_counter()
+    verts = oracle_step(sample)
+    dt = time.perf_counter() - t0
+    return {"value": verts / dt, "unit": "vertices/s", "cores": 1, "kind": "oracle",
+            "sample": sample["desc"], "seconds": round(dt, 2)}
+
+
+def run_reference(args):
+    import torch
+
+    import oracle
+    import workloads
+
+    rank, world, local = dist_info()
+    if rank != 0:  # the oracle runs once, on rank 0
+        return
+    oracle.build()
+    E, ME = args.edge, args.mesh_edge
+    dev = torch.device("cuda", local) if torch.cuda.is_available() else torch.device("cpu")
+    f_smooth = workloads.field_smooth(edge=E, seed=1, device=dev).reshape(-1)
+    f_noise = workloads.field_noise(edge=E, seed=1, device=dev).reshape(-1)
+    mask = workloads.mask_blobs(edge=E, seed=2, device=dev).reshape(-1)
+    sample = oracle_sample(f_smooth, f_noise, mask, E)
+    del f_smooth, f_noise, mask
+    for _ in range(args.warmup):
+        oracle_step(sample)
+    t0 = time.perf_counter()
+    verts = 0
+    for _ in range(args.steps):
+        verts += oracle_step(sample)
+    dt = time.perf_counter() - t0
+    value = verts / dt
+    out = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": dt / args.steps * 1e3,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {"workload": "CPU oracle on a bounded sample of the same workload", "sample": sample["desc"],
+                   "vertices_per_step": verts // max(1, args.steps)},
+        "cpu_baseline": {"value": value, "unit": "vertices/s", "cores": 1, "kind": "oracle",
+                         "sample": sample["desc"]},
+        "e2e": {"value": value, "unit": "vertices/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(out), flush=True)
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -30,6 +30,7 @@ __all__ = [
     "msc_compress", "msc_ms_id", "msc_segment", "msc_cc_mask", "msc_cc_mesh",
     "order", "steepest_grid", "steepest_csr", "compress", "ms_id", "segment", "cc_mask", "cc_mesh",
     "OP_ORDER", "OP_COMPRESS", "OP_MS_ID", "OP_SEGMENT", "OP_CC_MASK", "OP_CC_MESH",
+    "msc_launch_count", "msc_trace_enable", "msc_trace_reset", "msc_trace_collect",
 ]
 
 OK, ERR_ARG, ERR_WS, ERR_CUDA, ERR_NAN, ERR_NOT_CONVERGED, ERR_BUDGET, ERR_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
@@ -76,6 +77,10 @@ def load(build_if_missing: bool = False):
         "msc_segment": (ctypes.c_int, [P, Grid, P, P, P, P, P, P, SZ, P, P]),
         "msc_cc_mask": (ctypes.c_int, [P, Grid, I32, P, P, SZ, P, P]),
         "msc_cc_mesh": (ctypes.c_int, [P, P, I32, P, P, SZ, P, P]),
+        "msc_launch_count": (ctypes.c_ulonglong, []),
+        "msc_trace_enable": (None, [ctypes.c_int]),
+        "msc_trace_reset": (None, []),
+        "msc_trace_collect": (ctypes.c_int, [ctypes.c_char_p, SZ]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -155,6 +160,31 @@ def msc_cc_mask(mask, dims, conn, label, ws, ws_bytes, status, stream=None) -> i
 
 def msc_cc_mesh(row, col, n, label, ws, ws_bytes, status, stream=None) -> int:
     return load().msc_cc_mesh(_p(row), _p(col), n, _p(label), _p(ws), ws_bytes, _p(status), _stream(stream))
+
+
+def msc_launch_count() -> int:
+    return int(load().msc_launch_count())
+
+
+def msc_trace_enable(on: bool) -> None:
+    load().msc_trace_enable(1 if on else 0)
+
+
+def msc_trace_reset() -> None:
+    load().msc_trace_reset()
+
+
+def msc_trace_collect() -> dict:
+    """{label: (launches, total device ms)} of the launches recorded while
+    tracing was enabled (waits for them to finish)."""
+    import json
+
+    cap = 1 << 16
+    buf = ctypes.create_string_buffer(cap)
+    code = load().msc_trace_collect(buf, cap)
+    if code != OK:
+        raise MSCError(code, "msc_trace_collect")
+    return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
 
 
 # ---------------------------------------------------------------------------

@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmsc.so")
 
-SOURCES = ["sort.cu", "steepest.cu", "compress.cu", "msid.cu", "cc.cu", "msc_api.cu"]
+SOURCES = ["sort.cu", "steepest.cu", "compress.cu", "msid.cu", "cc.cu", "msc_api.cu", "trace.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]
 
@@ -32,7 +32,7 @@ def _nvcc() -> str:
 
 def _inputs():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC) if f.endswith((".cu", ".cuh", ".h", ".cpp"))]
-    files.append(os.path.join(INCLUDE, "msc.h"))
+    files += [os.path.join(INCLUDE, h) for h in os.listdir(INCLUDE) if h.endswith(".h")]
     return files
 
 

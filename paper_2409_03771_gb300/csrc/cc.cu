@@ -282,11 +282,20 @@ int run_cc_mask(const uint8_t* mask, msc_grid gd, int conn, int32_t* label, int3
     int occ = 1;
     MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_cc_local, kThreads, 0));
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)sms * std::max(occ, 1)));
-    k_cc_local<<<grid, kThreads, 0, s>>>(mask, g, label);
+    {
+        TraceScope ts_("cc.local", s);
+        k_cc_local<<<grid, kThreads, 0, s>>>(mask, g, label);
+    }
     MSC_LAUNCHED();
-    k_cc_merge<<<grid, kThreads, 0, s>>>(g, label, status);
+    {
+        TraceScope ts_("cc.merge", s);
+        k_cc_merge<<<grid, kThreads, 0, s>>>(g, label, status);
+    }
     MSC_LAUNCHED();
-    k_flatten<<<cc_grid_for(n), 256, 0, s>>>(label, n);
+    {
+        TraceScope ts_("cc.flatten", s);
+        k_flatten<<<cc_grid_for(n), 256, 0, s>>>(label, n);
+    }
     MSC_LAUNCHED();
     return MSC_OK;
 }
@@ -295,11 +304,20 @@ int run_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* labe
                 cudaStream_t s) {
     if (n <= 0) return MSC_OK;
     const int grid = cc_grid_for(n);
-    k_mesh_init<<<grid, 256, 0, s>>>(row, col, n, label, status);
+    {
+        TraceScope ts_("mesh.init", s);
+        k_mesh_init<<<grid, 256, 0, s>>>(row, col, n, label, status);
+    }
     MSC_LAUNCHED();
-    k_mesh_hook<<<grid, 256, 0, s>>>(row, col, n, label, status);
+    {
+        TraceScope ts_("mesh.hook", s);
+        k_mesh_hook<<<grid, 256, 0, s>>>(row, col, n, label, status);
+    }
     MSC_LAUNCHED();
-    k_flatten<<<grid, 256, 0, s>>>(label, n);
+    {
+        TraceScope ts_("mesh.flatten", s);
+        k_flatten<<<grid, 256, 0, s>>>(label, n);
+    }
     MSC_LAUNCHED();
     return MSC_OK;
 }

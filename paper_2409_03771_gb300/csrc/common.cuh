@@ -55,6 +55,22 @@ struct Device {
     int max_smem_optin = 0;
 };
 
+// Counts one kernel launch and, while tracing is on, brackets it with CUDA
+// events on its stream (see trace.cu).  Construct right before the launch
+// and let it go out of scope right after.
+class TraceScope {
+   public:
+    TraceScope(const char* label, cudaStream_t s);
+    ~TraceScope();
+    TraceScope(const TraceScope&) = delete;
+    TraceScope& operator=(const TraceScope&) = delete;
+
+   private:
+    const char* label_;
+    cudaStream_t stream_;
+    cudaEvent_t a_ = nullptr, b_ = nullptr;
+};
+
 // Properties of the current device (cached per device id).
 const Device& current_device();
 

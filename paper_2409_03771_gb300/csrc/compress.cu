@@ -205,10 +205,16 @@ int run_compress(int32_t* const* ptrs, int count, int32_t n, const CompressScrat
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)current_device().sms * std::max(occ, 1)));
     const int steps = compress_steps(n);
     for (int st = 0; st < steps; ++st) {
-        k_jump<<<dim3(gx, count), kThreads, 0, s>>>(pr, st, build_shift, status);
+        {
+            TraceScope ts_("compress.jump", s);
+            k_jump<<<dim3(gx, count), kThreads, 0, s>>>(pr, st, build_shift, status);
+        }
         MSC_LAUNCHED();
     }
-    k_jump_finish<<<1, 1, 0, s>>>(pr, count, steps - 1, status);
+    {
+        TraceScope ts_("compress.finish", s);
+        k_jump_finish<<<1, 1, 0, s>>>(pr, count, steps - 1, status);
+    }
     MSC_LAUNCHED();
     return MSC_OK;
 }

@@ -229,16 +229,31 @@ int run_ms_id(const int32_t* asc, const int32_t* desc, int32_t n, int32_t* ms, i
     }
     if (!counts_known) {
         MSC_TRY(cudaMemsetAsync(sc.ctl, 0, 4 * sizeof(uint32_t), s));
-        k_ms_prepare<<<grid_for(n), kThreads, 0, s>>>(asc, desc, n, sc.ctl, status);
+        {
+            TraceScope ts_("msid.prepare", s);
+            k_ms_prepare<<<grid_for(n), kThreads, 0, s>>>(asc, desc, n, sc.ctl, status);
+        }
         MSC_LAUNCHED();
     }
-    k_ms_setcap<<<1, 1, 0, s>>>(sc.ctl, n, sc.cap_max);
+    {
+        TraceScope ts_("msid.setcap", s);
+        k_ms_setcap<<<1, 1, 0, s>>>(sc.ctl, n, sc.cap_max);
+    }
     MSC_LAUNCHED();
-    k_ms_clear<<<grid_for(sc.cap_max, 4), kThreads, 0, s>>>(sc.table_keys, sc.ctl);
+    {
+        TraceScope ts_("msid.clear", s);
+        k_ms_clear<<<grid_for(sc.cap_max, 4), kThreads, 0, s>>>(sc.table_keys, sc.ctl);
+    }
     MSC_LAUNCHED();
-    k_ms_insert<<<grid_for(n), kThreads, 0, s>>>(asc, desc, n, sc.table_keys, sc.ctl, ms, status);
+    {
+        TraceScope ts_("msid.insert", s);
+        k_ms_insert<<<grid_for(n), kThreads, 0, s>>>(asc, desc, n, sc.table_keys, sc.ctl, ms, status);
+    }
     MSC_LAUNCHED();
-    k_ms_compact<<<grid_for(sc.cap_max, 4), kThreads, 0, s>>>(sc.table_keys, sc.ctl, sc.ukeys[0], sc.uvals[0], status);
+    {
+        TraceScope ts_("msid.compact", s);
+        k_ms_compact<<<grid_for(sc.cap_max, 4), kThreads, 0, s>>>(sc.table_keys, sc.ctl, sc.ukeys[0], sc.uvals[0], status);
+    }
     MSC_LAUNCHED();
     const int key_bits = ceil_log2((int64_t)n * (int64_t)n);
     bool in_alt = false;
@@ -246,9 +261,15 @@ int run_ms_id(const int32_t* asc, const int32_t* desc, int32_t n, int32_t* ms, i
                          reinterpret_cast<const int32_t*>(sc.ctl + 3), n, key_bits, sc.sort, status, s,
                          &in_alt);
     if (r) return r;
-    k_ms_rank<<<grid_for(n), kThreads, 0, s>>>(in_alt ? sc.uvals[1] : sc.uvals[0], sc.ctl, sc.table_vals, status);
+    {
+        TraceScope ts_("msid.rank", s);
+        k_ms_rank<<<grid_for(n), kThreads, 0, s>>>(in_alt ? sc.uvals[1] : sc.uvals[0], sc.ctl, sc.table_vals, status);
+    }
     MSC_LAUNCHED();
-    k_ms_lookup<<<grid_for(n / 4 + 1), kThreads, 0, s>>>(ms, n, sc.table_vals, sc.ctl, num_cells);
+    {
+        TraceScope ts_("msid.lookup", s);
+        k_ms_lookup<<<grid_for(n / 4 + 1), kThreads, 0, s>>>(ms, n, sc.table_vals, sc.ctl, num_cells);
+    }
     MSC_LAUNCHED();
     return MSC_OK;
 }

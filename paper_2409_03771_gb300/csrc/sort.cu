@@ -295,7 +295,7 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const PassArgs<KeyT> a) {
 }
 
 template <typename KeyT, bool FROM_F, bool TO_ORDER>
-int launch_pass(const PassArgs<KeyT>& a, int64_t max_n, cudaStream_t s) {
+int launch_pass(const PassArgs<KeyT>& a, int64_t max_n, cudaStream_t s, const char* label) {
     constexpr size_t smem = pass_smem_bytes<KeyT, !TO_ORDER>();
     auto kern = k_onesweep<KeyT, FROM_F, TO_ORDER>;
     static int configured_dev = -1;  // the attribute is set once per device
@@ -307,7 +307,10 @@ int launch_pass(const PassArgs<KeyT>& a, int64_t max_n, cudaStream_t s) {
     MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
     const int64_t ntiles = ceil_div(max_n, kSortTile);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)current_device().sms * std::max(occ, 1)));
-    kern<<<(unsigned)grid, kThreads, smem, s>>>(a);
+    {
+        TraceScope ts_(label, s);
+        kern<<<(unsigned)grid, kThreads, smem, s>>>(a);
+    }
     MSC_LAUNCHED();
     return MSC_OK;
 }
@@ -346,7 +349,10 @@ int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_
     if (n <= 0) return MSC_OK;
     int r = clear_scratch(sc, n, s);
     if (r) return r;
-    k_hist<uint32_t, true><<<hist_grid(n), 256, 0, s>>>(nullptr, f, n, nullptr, 4, sc.hist, status);
+    {
+        TraceScope ts_("order.hist", s);
+        k_hist<uint32_t, true><<<hist_grid(n), 256, 0, s>>>(nullptr, f, n, nullptr, 4, sc.hist, status);
+    }
     MSC_LAUNCHED();
     PassArgs<uint32_t> a{};
     a.n = n;
@@ -360,7 +366,7 @@ int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_
     a.shift = 0;
     a.tile_counter = sc.tile_counters + 0;
     a.epoch = 1;
-    if ((r = launch_pass<uint32_t, true, false>(a, n, s))) return r;
+    if ((r = launch_pass<uint32_t, true, false>(a, n, s, "order.pass_first"))) return r;
     // pass 1: a -> b ; pass 2: b -> a
     uint32_t* kin = key_a;
     int32_t* iin = id_a;
@@ -376,7 +382,7 @@ int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_
         a.shift = 8 * p;
         a.tile_counter = sc.tile_counters + p;
         a.epoch = (uint32_t)(p + 1);
-        if ((r = launch_pass<uint32_t, false, false>(a, n, s))) return r;
+        if ((r = launch_pass<uint32_t, false, false>(a, n, s, "order.pass"))) return r;
         std::swap(kin, kout);
         std::swap(iin, iout);
     }
@@ -390,7 +396,7 @@ int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_
     a.shift = 24;
     a.tile_counter = sc.tile_counters + 3;
     a.epoch = 4;
-    return launch_pass<uint32_t, false, true>(a, n, s);
+    return launch_pass<uint32_t, false, true>(a, n, s, "order.pass_last");
 }
 
 int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* keys_alt,
@@ -401,7 +407,10 @@ int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* ke
     const int npass = std::min(8, (key_bits + 7) / 8);
     int r = clear_scratch(sc, max_count, s);
     if (r) return r;
-    k_hist<unsigned long long, false><<<hist_grid(max_count), 256, 0, s>>>(keys, nullptr, max_count, d_count, npass, sc.hist, status);
+    {
+        TraceScope ts_("msid.sort_hist", s);
+        k_hist<unsigned long long, false><<<hist_grid(max_count), 256, 0, s>>>(keys, nullptr, max_count, d_count, npass, sc.hist, status);
+    }
     MSC_LAUNCHED();
     PassArgs<unsigned long long> a{};
     a.n = max_count;
@@ -421,7 +430,7 @@ int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* ke
         a.shift = 8 * p;
         a.tile_counter = sc.tile_counters + p;
         a.epoch = (uint32_t)(p + 1);
-        if ((r = launch_pass<unsigned long long, false, false>(a, max_count, s))) return r;
+        if ((r = launch_pass<unsigned long long, false, false>(a, max_count, s, "msid.sort_pass"))) return r;
         std::swap(kin, kout);
         std::swap(vin, vout);
     }

@@ -350,12 +350,18 @@ int run_steepest_grid(const int32_t* order, msc_grid gd, int32_t* asc, int32_t* 
         auto kern = packed ? k_steepest_tma<int32_t> : k_steepest_tma<int64_t>;
         MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)sms * std::max(occ, 1)));
-        kern<<<(unsigned)grid, kThreads, 0, s>>>(map, g, asc, desc, extrema, status);
+        {
+            TraceScope ts_("steepest.grid", s);
+            kern<<<(unsigned)grid, kThreads, 0, s>>>(map, g, asc, desc, extrema, status);
+        }
     } else {
         auto kern = packed ? k_steepest_ld<int32_t> : k_steepest_ld<int64_t>;
         MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)sms * std::max(occ, 1)));
-        kern<<<(unsigned)grid, kThreads, 0, s>>>(order, g, asc, desc, extrema);
+        {
+            TraceScope ts_("steepest.grid", s);
+            kern<<<(unsigned)grid, kThreads, 0, s>>>(order, g, asc, desc, extrema);
+        }
     }
     MSC_LAUNCHED();
     return MSC_OK;
@@ -366,7 +372,10 @@ int run_steepest_csr(const int32_t* order, const int32_t* row, const int32_t* co
     if (n <= 0) return MSC_OK;
     const int64_t want = ceil_div((int64_t)n * kCsrLanes, 256);
     const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)current_device().sms * 8));
-    k_steepest_csr<<<grid, 256, 0, s>>>(order, row, col, n, asc, desc, status);
+    {
+        TraceScope ts_("steepest.csr", s);
+        k_steepest_csr<<<grid, 256, 0, s>>>(order, row, col, n, asc, desc, status);
+    }
     MSC_LAUNCHED();
     return MSC_OK;
 }
