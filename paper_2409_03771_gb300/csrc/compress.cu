@@ -11,8 +11,9 @@
 // n >> build_shift vertices changed, the sweep also appends the changed
 // vertices to an active list (block-aggregated atomics) and the following
 // sweeps walk only that list -- the GPU counterpart of the paper's
-// per-thread active lists.  A change in the last sweep means a pointer
-// cycle: MSC_ERR_NOT_CONVERGED.
+// per-thread active lists.  A pointer cycle is reported as
+// MSC_ERR_NOT_CONVERGED: either a jump lands on its own vertex, or the last
+// sweep still changes something.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -38,8 +39,12 @@ struct JumpPair {
     int vec;  // int4 access allowed
 };
 
-// One jump of one vertex; returns true when d changed.
-__device__ __forceinline__ bool jump_one(const int32_t* p, int32_t n, int32_t& d, int32_t* status) {
+// One jump of vertex v (current pointer d); returns true when d changed.
+// In a forest a jump always lands on a strict ancestor, so landing on v
+// itself can only happen on a pointer cycle; in-place jumping can collapse
+// a cycle into such a self-loop, which would otherwise look converged.
+__device__ __forceinline__ bool jump_one(const int32_t* p, int32_t n, int32_t v, int32_t& d,
+                                         int32_t* status) {
     const int32_t u = d;
     if (u < 0) return false;
     if ((uint32_t)u >= (uint32_t)n) {
@@ -50,6 +55,10 @@ __device__ __forceinline__ bool jump_one(const int32_t* p, int32_t n, int32_t& d
     if (w == u) return false;
     if (w < 0) {
         record_error(status, MSC_ERR_ARG);
+        return false;
+    }
+    if (w == v) {
+        record_error(status, MSC_ERR_NOT_CONVERGED);
         return false;
     }
     d = w;
@@ -82,17 +91,18 @@ __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, 
             const int64_t v0 = c * kChunk + (int64_t)tid * 4;
             if (pr.vec && v0 + 3 < n) {
                 int4 d = *reinterpret_cast<const int4*>(p + v0);
-                ch |= jump_one(p, n, d.x, status) ? 1u : 0u;
-                ch |= jump_one(p, n, d.y, status) ? 2u : 0u;
-                ch |= jump_one(p, n, d.z, status) ? 4u : 0u;
-                ch |= jump_one(p, n, d.w, status) ? 8u : 0u;
+                const int32_t v = (int32_t)v0;
+                ch |= jump_one(p, n, v, d.x, status) ? 1u : 0u;
+                ch |= jump_one(p, n, v + 1, d.y, status) ? 2u : 0u;
+                ch |= jump_one(p, n, v + 2, d.z, status) ? 4u : 0u;
+                ch |= jump_one(p, n, v + 3, d.w, status) ? 8u : 0u;
                 if (ch) *reinterpret_cast<int4*>(p + v0) = d;
             } else {
 #pragma unroll
                 for (int j = 0; j < 4; ++j) {
                     if (v0 + j < n) {
                         int32_t d = p[v0 + j];
-                        if (jump_one(p, n, d, status)) {
+                        if (jump_one(p, n, (int32_t)(v0 + j), d, status)) {
                             p[v0 + j] = d;
                             ch |= 1u << j;
                         }
@@ -114,7 +124,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, 
                     if ((uint32_t)v >= (uint32_t)n) continue;
 #endif
                     int32_t d = p[v];
-                    if (jump_one(p, n, d, status)) {
+                    if (jump_one(p, n, v, d, status)) {
                         p[v] = d;
                         ch |= 1u << j;
                     }

@@ -154,6 +154,15 @@ def test_compress_cycle_is_reported(m):
     assert e.value.code == m.ERR_NOT_CONVERGED
 
 
+@pytest.mark.parametrize("cycle", [[1, 0], [1, 2, 0], [0, 2, 3, 1], [1, 2, 3, 4, 5, 6, 7, 0]])
+def test_compress_short_cycles_are_reported(m, cycle):
+    """In-place jumping can collapse a cycle into a self-loop; still an error."""
+    ptr = torch.tensor(cycle, dtype=torch.int32, device="cuda")
+    with pytest.raises(m.MSCError) as e:
+        m.compress(ptr)
+    assert e.value.code == m.ERR_NOT_CONVERGED
+
+
 def test_compress_bad_pointer_is_reported(m):
     ptr = torch.tensor([0, 0, 7, 2], dtype=torch.int32, device="cuda")
     with pytest.raises(m.MSCError) as e:
