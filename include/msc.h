@@ -54,6 +54,7 @@ extern "C" {
 #define MSC_ERR_NOT_CONVERGED (-5)
 #define MSC_ERR_BUDGET (-6)
 #define MSC_ERR_INTERNAL (-7)
+#define MSC_ERR_TOO_LARGE (-8)
 #define MSC_PENDING 1
 
 /* Regular grid: vertices per axis. */
@@ -122,6 +123,28 @@ MSC_API int msc_steepest_csr(const int32_t* order, const int32_t* row, const int
  *        after ceil(log2 n) + 2 sweeps. */
 MSC_API int msc_compress(int32_t* ptr, int32_t n, void* ws, size_t ws_bytes, int32_t* d_status,
                  void* stream);
+
+/* Path compression for callers that cannot allocate device memory.  The
+ * paper has no counterpart: this entry point exists for code that must not
+ * call cudaMalloc -- a host function enqueued on a stream (such callbacks
+ * may not make CUDA calls), a process whose device memory is owned by
+ * another allocator or a fixed budget (a serving runtime, a plugin inside a
+ * framework), or code that must not risk the device-wide synchronisation
+ * that allocating and freeing can cause.  It does what msc_compress does,
+ * with the same arguments minus the workspace, and allocates nothing (no
+ * cudaMalloc, cudaFree or allocating library routine).
+ *   n  at most MSC_NOALLOC_MAX_N; larger n returns MSC_ERR_TOO_LARGE.
+ * Scratch: a static device array of about 2 MiB (step counters and two
+ * active lists of MSC_NOALLOC_MAX_N / 16 + 1 entries), which every GPU that
+ * loads libmsc holds until the process exits.  All calls share it and it
+ * keeps the last call's contents (the counters are cleared on every call):
+ * calls that overlap on the GPU -- on different streams, or on different
+ * host threads without ordering -- race on it and must not be issued.
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress with that device current); make that first call
+ * before any stream capture. */
+#define MSC_NOALLOC_MAX_N (1 << 22)
+MSC_API int msc_compress_noalloc(int32_t* ptr, int32_t n, int32_t* d_status, void* stream);
 
 /* Dense Morse-Smale cell ids (section "Ascending and Descending
  * Segmentation": vertices whose steepest descent and ascent end in the

@@ -27,13 +27,15 @@ from . import _build
 __all__ = [
     "MSCError", "load", "lib_path",
     "msc_workspace_bytes", "msc_status_string", "msc_order", "msc_steepest_grid", "msc_steepest_csr",
-    "msc_compress", "msc_ms_id", "msc_segment", "msc_cc_mask", "msc_cc_mesh",
+    "msc_compress", "msc_compress_noalloc", "msc_ms_id", "msc_segment", "msc_cc_mask", "msc_cc_mesh",
     "order", "steepest_grid", "steepest_csr", "compress", "ms_id", "segment", "cc_mask", "cc_mesh",
     "OP_ORDER", "OP_COMPRESS", "OP_MS_ID", "OP_SEGMENT", "OP_CC_MASK", "OP_CC_MESH",
     "msc_launch_count", "msc_trace_enable", "msc_trace_reset", "msc_trace_collect",
 ]
 
 OK, ERR_ARG, ERR_WS, ERR_CUDA, ERR_NAN, ERR_NOT_CONVERGED, ERR_BUDGET, ERR_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
+ERR_TOO_LARGE = -8
+NOALLOC_MAX_N = 1 << 22
 PENDING = 1
 OP_ORDER, OP_COMPRESS, OP_MS_ID, OP_SEGMENT, OP_CC_MASK, OP_CC_MESH = 1, 2, 3, 4, 5, 6
 
@@ -73,6 +75,7 @@ def load(build_if_missing: bool = False):
         "msc_steepest_grid": (ctypes.c_int, [P, Grid, P, P, P]),
         "msc_steepest_csr": (ctypes.c_int, [P, P, P, I32, P, P, P, P]),
         "msc_compress": (ctypes.c_int, [P, I32, P, SZ, P, P]),
+        "msc_compress_noalloc": (ctypes.c_int, [P, I32, P, P]),
         "msc_ms_id": (ctypes.c_int, [P, P, I32, P, P, P, SZ, P, P]),
         "msc_segment": (ctypes.c_int, [P, Grid, P, P, P, P, P, P, SZ, P, P]),
         "msc_cc_mask": (ctypes.c_int, [P, Grid, I32, P, P, SZ, P, P]),
@@ -141,6 +144,11 @@ def msc_steepest_csr(order, row, col, n, asc_ptr, desc_ptr, status, stream=None)
 
 def msc_compress(ptr, n, ws, ws_bytes, status, stream=None) -> int:
     return load().msc_compress(_p(ptr), n, _p(ws), ws_bytes, _p(status), _stream(stream))
+
+
+def msc_compress_noalloc(ptr, n, status, stream=None) -> int:
+    """Path compression with no workspace (static device scratch, n <= NOALLOC_MAX_N)."""
+    return load().msc_compress_noalloc(_p(ptr), n, _p(status), _stream(stream))
 
 
 def msc_ms_id(asc, desc, n, ms, num_cells, ws, ws_bytes, status, stream=None) -> int:

@@ -17,6 +17,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "compress.cuh"
 
@@ -230,3 +231,60 @@ int run_compress(int32_t* const* ptrs, int count, int32_t n, const CompressScrat
 }
 
 }  // namespace msc
+
+// ----------------------------------------------------------------------------
+// msc_compress_noalloc: the same compression for callers that cannot
+// allocate device memory.  Its scratch (the step counters and the two active
+// lists) is this file-scope array, which every GPU that loads the library
+// holds until the process exits.  The active list is built once at most
+// n/16 vertices changed, so two lists of n_max/16 + 1 entries suffice.
+
+namespace {
+
+constexpr int64_t kNoAllocMaxN = MSC_NOALLOC_MAX_N;
+constexpr int kNoAllocBuildShift = 4;
+constexpr int64_t kNoAllocListCap = (kNoAllocMaxN >> kNoAllocBuildShift) + 1;
+constexpr size_t kNoAllocCtlBytes = (sizeof(msc::JumpCtl) + 255) & ~size_t(255);
+constexpr size_t kNoAllocBytes = kNoAllocCtlBytes + 2 * kNoAllocListCap * sizeof(int32_t);
+
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoAllocBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device with that
+// device current (a host-side use of the symbol's name is not a device
+// address).
+int noalloc_scratch(void** out) {
+    static void* addr[64] = {};
+    static std::mutex mu;
+    int dev = 0;
+    MSC_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return MSC_ERR_ARG;
+    std::lock_guard<std::mutex> lock(mu);
+    if (!addr[dev]) {
+        void* p = nullptr;
+        MSC_TRY(cudaGetSymbolAddress(&p, g_noalloc_scratch));
+        addr[dev] = p;
+    }
+    *out = addr[dev];
+    return MSC_OK;
+}
+
+}  // namespace
+
+extern "C" MSC_API int msc_compress_noalloc(int32_t* ptr, int32_t n, int32_t* d_status, void* stream) {
+    if (n < 0 || !d_status || (n > 0 && !ptr)) return MSC_ERR_ARG;
+    if ((int64_t)n > kNoAllocMaxN) return MSC_ERR_TOO_LARGE;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    void* base = nullptr;
+    int r = noalloc_scratch(&base);
+    if (r) return r;
+    MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
+    if (n == 0) return MSC_OK;
+    msc::CompressScratch sc;
+    sc.ctl = static_cast<msc::JumpCtl*>(base);  // zeroed by run_compress
+    sc.list_cap = kNoAllocListCap;
+    sc.lists = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(base) + kNoAllocCtlBytes);
+    msc::CompressTune tune;
+    tune.build_shift = kNoAllocBuildShift;
+    int32_t* arr[1] = {ptr};
+    return msc::run_compress(arr, 1, n, sc, d_status, s, tune);
+}

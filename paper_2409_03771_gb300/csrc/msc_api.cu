@@ -117,6 +117,7 @@ const char* msc_status_string(int code) {
         case MSC_ERR_NOT_CONVERGED: return "pointer jumping did not converge (pointer cycle)";
         case MSC_ERR_BUDGET: return "request exceeds the memory budget";
         case MSC_ERR_INTERNAL: return "internal error";
+        case MSC_ERR_TOO_LARGE: return "size exceeds the static scratch of the no-allocation entry point";
         case MSC_PENDING: return "pending";
         default: return "unknown status";
     }
