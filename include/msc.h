@@ -120,7 +120,8 @@ MSC_API int msc_steepest_csr(const int32_t* order, const int32_t* row, const int
  *        paper's -1 outside a feature mask) and are left as they are.
  *        An active entry pointing outside [0, n) or at an inactive entry
  *        sets MSC_ERR_ARG; a pointer cycle sets MSC_ERR_NOT_CONVERGED
- *        after ceil(log2 n) + 2 sweeps. */
+ *        (every sweep advances each pointer by up to three hops; at most
+ *        ceil(log4 n) + 2 sweeps are made). */
 MSC_API int msc_compress(int32_t* ptr, int32_t n, void* ws, size_t ws_bytes, int32_t* d_status,
                  void* stream);
 

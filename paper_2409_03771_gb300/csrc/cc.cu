@@ -56,10 +56,15 @@ __device__ __forceinline__ void cc_tile_coords(const CcGrid& g, int64_t t, int& 
 __constant__ int8_t c_pos[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0},
                                    {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
 
-__device__ __forceinline__ int find_s(const int* L, int x) {
+// Root of x in a shared-memory forest whose entries point at smaller
+// local indices, halving the path on the way (atomicMin: never undoes a
+// hook made by another thread).
+__device__ __forceinline__ int find_s(int* L, int x) {
     int p = L[x];
     while (p != x) {
-        x = p;
+        const int gp = L[p];
+        if (gp != p) atomicMin(&L[x], gp);
+        x = gp;
         p = L[x];
     }
     return x;
@@ -216,46 +221,111 @@ __global__ void __launch_bounds__(kThreads) k_cc_merge(const CcGrid g, int32_t* 
     }
 }
 
-__global__ void k_flatten(int32_t* label, int64_t n) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t l = label[v];
-        if (l < 0) continue;
-        const int32_t r = find_g(label, l);
-        if (r != l) atomicMin(label + v, r);
+// Pointer jumping to the roots.  A thread takes 8 labels, lane-consecutive
+// (label c*2048 + j*256 + tid), and follows their chains hop by hop
+// together: 8 independent gathers in flight, and the 32 lanes of each
+// gather read neighbouring labels, whose roots are mostly shared.  The few
+// chains still open after kFlatHops hops finish one by one.  Once every
+// hook is done the root reached is the component minimum, so a plain store
+// of it cannot lose anything.
+constexpr int kFlatPer = 8;
+constexpr int kFlatHops = 4;
+constexpr int kFlatThreads = 256;
+
+__global__ void __launch_bounds__(kFlatThreads) k_flatten(int32_t* label, int64_t n) {
+    constexpr int64_t kChunk = (int64_t)kFlatThreads * kFlatPer;
+    for (int64_t c = blockIdx.x; c * kChunk < n; c += gridDim.x) {
+        int32_t l[kFlatPer], r[kFlatPer];
+        uint32_t open = 0;
+#pragma unroll
+        for (int j = 0; j < kFlatPer; ++j) {
+            const int64_t v = c * kChunk + (int64_t)j * kFlatThreads + threadIdx.x;
+            l[j] = v < n ? label[v] : -1;
+            r[j] = l[j];
+            open |= (l[j] >= 0 ? 1u : 0u) << j;
+        }
+#pragma unroll
+        for (int h = 0; h < kFlatHops; ++h) {
+            int32_t w[kFlatPer];
+#pragma unroll
+            for (int j = 0; j < kFlatPer; ++j) w[j] = (open >> j & 1u) ? ld_volatile_s32(label + r[j]) : 0;
+#pragma unroll
+            for (int j = 0; j < kFlatPer; ++j)
+                if (open >> j & 1u) {
+                    if (w[j] == r[j]) open &= ~(1u << j);
+                    else r[j] = w[j];
+                }
+        }
+#pragma unroll
+        for (int j = 0; j < kFlatPer; ++j)
+            if (open >> j & 1u) r[j] = find_g(label, r[j]);
+#pragma unroll
+        for (int j = 0; j < kFlatPer; ++j) {
+            const int64_t v = c * kChunk + (int64_t)j * kFlatThreads + threadIdx.x;
+            if (v < n && r[j] != l[j]) label[v] = r[j];
+        }
     }
 }
 
 // ----------------------------------------------------------------------------
 // mesh
 
-__global__ void k_mesh_init(const int32_t* __restrict__ row, const int32_t* __restrict__ col,
-                            int32_t n, int32_t* label, int32_t* status) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
-        int32_t m = (int32_t)v;
-        const int32_t e1 = row[v + 1];
-        for (int32_t e = row[v]; e < e1; ++e) {
-            const int32_t u = col[e];
-            if ((uint32_t)u >= (uint32_t)n) {
-                record_error(status, MSC_ERR_ARG);
-                continue;
+// Mesh kernels: 8 lanes per vertex, each lane taking every 8th entry of
+// the row, so a row's column indices are read as contiguous 32-byte runs.
+constexpr int kRowLanes = 8;
+
+__global__ void __launch_bounds__(256) k_mesh_init(const int32_t* __restrict__ row,
+                                                   const int32_t* __restrict__ col, int32_t n,
+                                                   int32_t* label, int32_t* status) {
+    const int sub = threadIdx.x & (kRowLanes - 1);
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    constexpr int kPerWarp = 32 / kRowLanes;
+    for (int64_t wbase = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32) * kPerWarp; wbase < n;
+         wbase += warps * kPerWarp) {
+        const int64_t v = wbase + (threadIdx.x & 31) / kRowLanes;
+        int32_t m = INT32_MAX;
+        if (v < n) {
+            m = (int32_t)v;
+            const int32_t e1 = row[v + 1];
+            for (int32_t e = row[v] + sub; e < e1; e += kRowLanes) {
+                const int32_t u = col[e];
+                if ((uint32_t)u >= (uint32_t)n) {
+                    record_error(status, MSC_ERR_ARG);
+                    continue;
+                }
+                m = u < m ? u : m;
             }
-            m = u < m ? u : m;
         }
-        label[v] = m;
+#pragma unroll
+        for (int o = kRowLanes / 2; o > 0; o >>= 1) {
+            const int32_t t = __shfl_xor_sync(0xffffffffu, m, o);
+            m = t < m ? t : m;
+        }
+        if (v < n && sub == 0) label[v] = m;
     }
 }
 
-__global__ void k_mesh_hook(const int32_t* __restrict__ row, const int32_t* __restrict__ col,
-                            int32_t n, int32_t* label, int32_t* status) {
-    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n;
-         v += (int64_t)gridDim.x * blockDim.x) {
+// Union every edge (v, u) with u < v, after label[] holds, for every v, the
+// smallest of v and its neighbours.  The root of v is found once per row.
+__global__ void __launch_bounds__(256) k_mesh_hook(const int32_t* __restrict__ row,
+                                                   const int32_t* __restrict__ col, int32_t n,
+                                                   int32_t* label, int32_t* status) {
+    const int lane = threadIdx.x & 31, sub = lane & (kRowLanes - 1);
+    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) / 32;
+    constexpr int kPerWarp = 32 / kRowLanes;
+    for (int64_t wbase = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32) * kPerWarp; wbase < n;
+         wbase += warps * kPerWarp) {
+        const int64_t v = wbase + lane / kRowLanes;
+        int32_t rv = 0;
+        if (v < n && sub == 0) rv = find_g(label, (int32_t)v);
+        rv = __shfl_sync(0xffffffffu, rv, lane & ~(kRowLanes - 1));
+        if (v >= n) continue;
         const int32_t e1 = row[v + 1];
-        for (int32_t e = row[v]; e < e1; ++e) {
+        for (int32_t e = row[v] + sub; e < e1; e += kRowLanes) {
             const int32_t u = col[e];
             if ((uint32_t)u >= (uint32_t)v) continue;  // each edge once (u < v); bad u skipped
-            union_g(label, (int32_t)v, u, status);
+            if (ld_volatile_s32(label + u) == rv) continue;  // already hooked to v's root
+            union_g(label, rv, u, status);
         }
     }
 }
@@ -294,7 +364,7 @@ int run_cc_mask(const uint8_t* mask, msc_grid gd, int conn, int32_t* label, int3
     MSC_LAUNCHED();
     {
         TraceScope ts_("cc.flatten", s);
-        k_flatten<<<cc_grid_for(n), 256, 0, s>>>(label, n);
+        k_flatten<<<cc_grid_for(ceil_div(n, kFlatPer)), kFlatThreads, 0, s>>>(label, n);
     }
     MSC_LAUNCHED();
     return MSC_OK;
@@ -316,7 +386,7 @@ int run_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* labe
     MSC_LAUNCHED();
     {
         TraceScope ts_("mesh.flatten", s);
-        k_flatten<<<grid, 256, 0, s>>>(label, n);
+        k_flatten<<<cc_grid_for(ceil_div(n, kFlatPer)), kFlatThreads, 0, s>>>(label, n);
     }
     MSC_LAUNCHED();
     return MSC_OK;

@@ -1,18 +1,21 @@
 // Path compression by pointer doubling (Alg. 1 compression loop): every
 // active vertex v does u <- d[v], w <- d[u]; if u = w it is finished,
 // otherwise d[v] <- w.  As in the paper the update is in place: a read of
-// d[u] may already see this sweep's write, which only lengthens the jump,
-// so ceil(log2 L) + 1 sweeps finish a longest path of L vertices.
+// d[u] may already see this sweep's write, which only lengthens the jump.
 //
-// GPU form: one launch per sweep over all vertices (int4 loads, four
-// vertices per thread), launched ceil(log2 n) + 2 times.  Each sweep counts
+// GPU form: one launch per sweep over all vertices (eight vertices per
+// thread, lane-consecutive).  Each vertex follows up to three hops per sweep
+// (d[v] <- d[d[d[d[v]]]]), so a sweep at least quadruples every pointer's
+// reach for the same 8 bytes of pointer read and write per vertex; the
+// extra reads mostly hit the cache.  Launched ceil(log4 n) + 2 times.
+// Each sweep counts
 // the vertices it changed; a sweep whose predecessor changed nothing
 // returns at once, so no host synchronisation is needed.  Once at most
 // n >> build_shift vertices changed, the sweep also appends the changed
 // vertices to an active list (block-aggregated atomics) and the following
 // sweeps walk only that list -- the GPU counterpart of the paper's
 // per-thread active lists.  A pointer cycle is reported as
-// MSC_ERR_NOT_CONVERGED: either a jump lands on its own vertex, or the last
+// MSC_ERR_NOT_CONVERGED: either a hop lands on its own vertex, or the last
 // sweep still changes something.
 #include <cuda_runtime.h>
 
@@ -25,7 +28,6 @@ namespace msc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kChunk = kThreads * 4;
 
 struct JumpArray {
     int32_t* p;
@@ -37,38 +39,63 @@ struct JumpArray {
 struct JumpPair {
     JumpArray a[2];
     int32_t n;
-    int vec;  // int4 access allowed
 };
 
-// One jump of vertex v (current pointer d); returns true when d changed.
-// In a forest a jump always lands on a strict ancestor, so landing on v
-// itself can only happen on a pointer cycle; in-place jumping can collapse
-// a cycle into such a self-loop, which would otherwise look converged.
-__device__ __forceinline__ bool jump_one(const int32_t* p, int32_t n, int32_t v, int32_t& d,
-                                         int32_t* status) {
-    const int32_t u = d;
-    if (u < 0) return false;
-    if ((uint32_t)u >= (uint32_t)n) {
-        record_error(status, MSC_ERR_ARG);
-        return false;
+constexpr int kHops = 3;  // pointer hops followed per vertex and sweep
+constexpr int kPerThread = 8;  // vertices per thread and chunk
+constexpr int kChunkV = kThreads * kPerThread;
+
+// Up to kHops hops for each of a thread's vertices vid[j] (current
+// pointers d[j]); bit j of the result is set when d[j] changed.  The hops
+// advance all vertices together, so a thread keeps kPerThread independent
+// gathers in flight instead of walking one chain at a time.  Every value
+// read is an ancestor of the vertex on its path, so in-place reads of
+// pointers already moved in this sweep only lengthen the jump: after s
+// sweeps a vertex has advanced at least (kHops + 1)^s steps.  In a forest a
+// hop always lands on a strict ancestor, so landing on the vertex itself
+// can only happen on a pointer cycle (in-place jumping can collapse a
+// cycle into such a self-loop, which would otherwise look converged).
+__device__ __forceinline__ uint32_t jump_group(const int32_t* p, int32_t n, const int32_t (&vid)[kPerThread],
+                                               int32_t (&d)[kPerThread], uint32_t valid, int32_t* status) {
+    uint32_t live = 0, moved = 0;
+#pragma unroll
+    for (int j = 0; j < kPerThread; ++j) {
+        if (!(valid >> j & 1u) || d[j] < 0) continue;
+        if ((uint32_t)d[j] >= (uint32_t)n) {
+            record_error(status, MSC_ERR_ARG);
+            continue;
+        }
+        live |= 1u << j;
     }
-    const int32_t w = p[u];
-    if (w == u) return false;
-    if (w < 0) {
-        record_error(status, MSC_ERR_ARG);
-        return false;
+#pragma unroll
+    for (int h = 0; h < kHops; ++h) {
+        int32_t w[kPerThread];
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j) w[j] = (live >> j & 1u) ? p[d[j]] : 0;
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j) {
+            if (!(live >> j & 1u)) continue;
+            const int32_t u = d[j];
+            if (w[j] == u) {
+                live &= ~(1u << j);  // u is a root: done
+            } else if ((uint32_t)w[j] >= (uint32_t)n) {
+                record_error(status, MSC_ERR_ARG);  // out of range or inactive target
+                live &= ~(1u << j);
+            } else if (w[j] == vid[j]) {
+                record_error(status, MSC_ERR_NOT_CONVERGED);
+                live &= ~(1u << j);
+            } else {
+                d[j] = w[j];
+                moved |= 1u << j;
+            }
+        }
     }
-    if (w == v) {
-        record_error(status, MSC_ERR_NOT_CONVERGED);
-        return false;
-    }
-    d = w;
-    return true;
+    return moved;
 }
 
 __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, int build_shift,
                                                    int32_t* status) {
-    const JumpArray A = pr.a[blockIdx.y];
+    const JumpArray A = blockIdx.y ? pr.a[1] : pr.a[0];
     const int32_t n = pr.n;
     int32_t* p = A.p;
     const uint32_t prev = step == 0 ? (uint32_t)n : A.ctl->cnt[step - 1];
@@ -83,55 +110,44 @@ __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, 
     __shared__ uint32_t s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t total = from_list ? (int64_t)prev : (int64_t)n;
-    const int64_t nchunks = (total + kChunk - 1) / kChunk;
+    const int64_t nchunks = (total + kChunkV - 1) / kChunkV;
     uint32_t changed_total = 0;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        int32_t vid[4];
-        uint32_t ch = 0;
+        int32_t vid[kPerThread], d[kPerThread];
+        uint32_t valid = 0, ch;
+        // element j of the thread is vertex (or list entry) c*chunk + j*256 + tid:
+        // the 32 lanes of every load, gather and store touch consecutive
+        // vertices, whose pointers (and the pointers' pointers) are
+        // neighbours, so each warp access covers few sectors
         if (!from_list) {
-            const int64_t v0 = c * kChunk + (int64_t)tid * 4;
-            if (pr.vec && v0 + 3 < n) {
-                int4 d = *reinterpret_cast<const int4*>(p + v0);
-                const int32_t v = (int32_t)v0;
-                ch |= jump_one(p, n, v, d.x, status) ? 1u : 0u;
-                ch |= jump_one(p, n, v + 1, d.y, status) ? 2u : 0u;
-                ch |= jump_one(p, n, v + 2, d.z, status) ? 4u : 0u;
-                ch |= jump_one(p, n, v + 3, d.w, status) ? 8u : 0u;
-                if (ch) *reinterpret_cast<int4*>(p + v0) = d;
-            } else {
+            const int64_t v0 = c * kChunkV + tid;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    if (v0 + j < n) {
-                        int32_t d = p[v0 + j];
-                        if (jump_one(p, n, (int32_t)(v0 + j), d, status)) {
-                            p[v0 + j] = d;
-                            ch |= 1u << j;
-                        }
-                    }
-                }
+            for (int j = 0; j < kPerThread; ++j) {
+                const int64_t v = v0 + (int64_t)j * kThreads;
+                vid[j] = (int32_t)v;
+                d[j] = v < n ? p[v] : -1;
+                valid |= (v < n ? 1u : 0u) << j;
             }
-#pragma unroll
-            for (int j = 0; j < 4; ++j) vid[j] = (int32_t)(v0 + j);
         } else {
 #pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                const int64_t i = c * kChunk + (int64_t)j * kThreads + tid;
+            for (int j = 0; j < kPerThread; ++j) {
+                const int64_t i = c * kChunkV + (int64_t)j * kThreads + tid;
                 vid[j] = -1;
                 if (i < total) {
                     const int32_t v = in_list[i];
-                    vid[j] = v;
-                    MSC_GUARD((uint32_t)v < (uint32_t)n, status, -121) {}
-#ifdef MSC_DEBUG_BOUNDS
-                    if ((uint32_t)v >= (uint32_t)n) continue;
-#endif
-                    int32_t d = p[v];
-                    if (jump_one(p, n, v, d, status)) {
-                        p[v] = d;
-                        ch |= 1u << j;
+                    MSC_GUARD((uint32_t)v < (uint32_t)n, status, -121) {
+                        vid[j] = v;
+                        valid |= 1u << j;
                     }
                 }
             }
+#pragma unroll
+            for (int j = 0; j < kPerThread; ++j) d[j] = (valid >> j & 1u) ? p[vid[j]] : -1;
         }
+        ch = jump_group(p, n, vid, d, valid, status);
+#pragma unroll
+        for (int j = 0; j < kPerThread; ++j)
+            if (ch >> j & 1u) p[vid[j]] = d[j];
         const uint32_t cnt = __popc(ch);
         changed_total += cnt;
         if (build) {  // append the changed vertices; trip count is block-uniform
@@ -155,7 +171,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, 
             __syncthreads();
             uint32_t off = s_base + s_warp[warp] + incl - cnt;
 #pragma unroll
-            for (int j = 0; j < 4; ++j)
+            for (int j = 0; j < kPerThread; ++j)
                 if (ch & (1u << j)) {
                     MSC_GUARD(off < (uint32_t)n / 2 + 1, status, -122)
                     out_list[off] = vid[j];
@@ -178,7 +194,13 @@ __global__ void k_jump_finish(const JumpPair pr, int count, int last, int32_t* s
 
 }  // namespace
 
-int compress_steps(int64_t n) { return std::min(kMaxJumpSteps, ceil_log2(std::max<int64_t>(n, 2)) + 2); }
+// Sweeps for n vertices: enough for a path of n vertices at a (kHops+1)-fold
+// advance per sweep, plus two; more are needed only by a pointer cycle.
+int compress_steps(int64_t n) {
+    int s = 0;
+    for (int64_t reach = 1; reach < std::max<int64_t>(n, 2); reach *= (kHops + 1)) ++s;
+    return std::min(kMaxJumpSteps, s + 2);
+}
 
 static int64_t list_capacity(int64_t n) { return n / 2 + 1; }
 
@@ -201,18 +223,16 @@ int run_compress(int32_t* const* ptrs, int count, int32_t n, const CompressScrat
     MSC_TRY(cudaMemsetAsync(sc.ctl, 0, sizeof(JumpCtl) * count, s));
     JumpPair pr{};
     pr.n = n;
-    pr.vec = 1;
     for (int i = 0; i < count; ++i) {
         pr.a[i].p = ptrs[i];
         pr.a[i].ctl = sc.ctl + i;
         pr.a[i].list0 = sc.lists + (size_t)i * 2 * sc.list_cap;
         pr.a[i].list1 = pr.a[i].list0 + sc.list_cap;
-        if ((uintptr_t)ptrs[i] % 16 != 0) pr.vec = 0;
     }
     const int build_shift = std::max(1, std::min(tune.build_shift, 30));
     int occ = 1;
     MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jump, kThreads, 0));
-    const int64_t chunks = ceil_div(n, kChunk);
+    const int64_t chunks = ceil_div(n, kChunkV);
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)current_device().sms * std::max(occ, 1)));
     const int steps = compress_steps(n);
     for (int st = 0; st < steps; ++st) {

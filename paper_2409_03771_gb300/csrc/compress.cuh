@@ -18,8 +18,8 @@ struct CompressTune {
     int build_shift = 3;  // build the active list once <= n >> build_shift changed
 };
 
-// Sweeps launched for n vertices: ceil(log2 n) + 2 (enough for any forest;
-// more are needed only by a pointer cycle).
+// Sweeps launched for n vertices: ceil(log4 n) + 2 (enough for any forest
+// at a fourfold advance per sweep; more are needed only by a cycle).
 int compress_steps(int64_t n);
 
 // Workspace pieces for `count` arrays of n entries.

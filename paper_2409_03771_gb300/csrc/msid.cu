@@ -6,8 +6,9 @@
 // 1. A linear-probing hash table de-duplicates the pair keys
 //    asc * n + desc.  Its capacity is a power of two >= 2 * min(n,
 //    #minima * #maxima), chosen on the device, so smooth fields (few
-//    extrema) use a table that lives in L2.  Lanes of a warp holding the
-//    same key (neighbouring vertices usually share a cell) probe once.
+//    extrema) use a table that lives in L2.  Within a warp, a run of
+//    consecutive vertices with the same key (neighbours usually share a
+//    cell) probes once.
 //    Each vertex keeps its slot in `ms` for now.
 // 2. The occupied slots are compacted and radix-sorted by key.
 // 3. table_vals[slot] = rank; ms[v] = table_vals[ms[v]].
@@ -22,6 +23,8 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr unsigned long long kEmpty = ~0ull;
+constexpr uint32_t kSpread = 64;  // random spread of a pair around its home slot
+constexpr uint32_t kCacheResidentSlots = 1u << 20;  // 8 MiB of keys: plain random hashing
 
 __device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
     // 64-bit finaliser of MurmurHash3
@@ -78,9 +81,22 @@ __global__ void k_ms_clear(unsigned long long* keys, const uint32_t* ctl) {
         keys[i] = kEmpty;
 }
 
+// Home slot of a pair in a table too big for the cache: proportional to
+// its minimum's id plus a small random spread.  The minimum of a vertex lies near the vertex, so the
+// vertices of a warp, and the warps in flight, probe a narrow band of the
+// table (L2 hits instead of random DRAM sectors), and the slots of sorted
+// pairs are nearly increasing, which keeps the rank writes and the final
+// lookups almost sequential too.
+__device__ __forceinline__ uint32_t home_slot(uint32_t asc, unsigned long long key, uint32_t cap,
+                                              int32_t n) {
+    if (cap <= kCacheResidentSlots) return (uint32_t)mix64(key) & (cap - 1);  // fits in cache: spread
+    const uint32_t base = (uint32_t)(((unsigned long long)asc * cap) / (unsigned long long)n);
+    return (base + (uint32_t)(mix64(key) & (kSpread - 1))) & (cap - 1);
+}
+
 __device__ __forceinline__ uint32_t probe_insert(unsigned long long* keys, uint32_t cap,
-                                                 unsigned long long key, int32_t* status) {
-    uint32_t h = (uint32_t)mix64(key) & (cap - 1);
+                                                 unsigned long long key, uint32_t home, int32_t* status) {
+    uint32_t h = home;
     for (uint32_t i = 0; i < cap; ++i) {
         const unsigned long long k = keys[h];
         if (k == key) return h;
@@ -105,16 +121,23 @@ __global__ void __launch_bounds__(kThreads) k_ms_insert(const int32_t* __restric
         const bool valid = v < n;
         unsigned long long key = kEmpty - 1 - lane;  // distinct per idle lane
         if (valid) key = (unsigned long long)(uint32_t)asc[v] * (unsigned long long)n + (uint32_t)desc[v];
-        const uint32_t peers = __match_any_sync(0xffffffffu, key);
-        const int leader = __ffs(peers) - 1;
+        // neighbouring vertices usually share their cell: only the first lane
+        // of each run of equal keys probes, the others take its slot
+        const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+        const bool head = lane == 0 || key != prev;
+        const uint32_t heads = __ballot_sync(0xffffffffu, head);
+        const int my_head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
         uint32_t slot = 0;
-        if (valid && lane == leader) slot = probe_insert(keys, cap, key, status);
-        slot = __shfl_sync(0xffffffffu, slot, leader);
+        if (valid && head) slot = probe_insert(keys, cap, key, home_slot((uint32_t)asc[v], key, cap, n), status);
+        slot = __shfl_sync(0xffffffffu, slot, my_head);
         if (valid) ms[v] = (int32_t)slot;
     }
 }
 
-// Compact occupied slots: (key, slot) pairs, block-aggregated appends.
+// Compact occupied slots into (key, slot) pairs: each thread scans 8
+// consecutive slots with 16-byte loads; one atomic append per block chunk.
+constexpr int kCompactPer = 8;
+
 __global__ void __launch_bounds__(kThreads) k_ms_compact(const unsigned long long* __restrict__ keys,
                                                          uint32_t* ctl, unsigned long long* ukeys,
                                                          int32_t* uvals, int32_t* status) {
@@ -122,13 +145,32 @@ __global__ void __launch_bounds__(kThreads) k_ms_compact(const unsigned long lon
     __shared__ uint32_t s_base;
     const int64_t cap = ctl[2];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t nchunks = (cap + kThreads - 1) / kThreads;
+    constexpr int64_t kChunkSlots = (int64_t)kThreads * kCompactPer;
+    const int64_t nchunks = (cap + kChunkSlots - 1) / kChunkSlots;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        const int64_t i = c * kThreads + tid;
-        const unsigned long long k = i < cap ? keys[i] : kEmpty;
-        const bool keep = k != kEmpty;
-        const uint32_t m = __ballot_sync(0xffffffffu, keep);
-        if (lane == 0) s_warp[warp] = __popc(m);
+        const int64_t i0 = c * kChunkSlots + (int64_t)tid * kCompactPer;
+        unsigned long long k[kCompactPer];
+        if (i0 + kCompactPer <= cap) {  // cap is a power of two >= 64: whole groups
+#pragma unroll
+            for (int q = 0; q < kCompactPer / 2; ++q) {
+                const ulonglong2 v = reinterpret_cast<const ulonglong2*>(keys + i0)[q];
+                k[2 * q] = v.x;
+                k[2 * q + 1] = v.y;
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kCompactPer; ++j) k[j] = i0 + j < cap ? keys[i0 + j] : kEmpty;
+        }
+        uint32_t cnt = 0;
+#pragma unroll
+        for (int j = 0; j < kCompactPer; ++j) cnt += k[j] != kEmpty;
+        uint32_t incl = cnt;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) s_warp[warp] = incl;
         __syncthreads();
         if (tid == 0) {
             uint32_t run = 0;
@@ -140,11 +182,15 @@ __global__ void __launch_bounds__(kThreads) k_ms_compact(const unsigned long lon
             s_base = run ? atomicAdd(&ctl[3], run) : 0u;
         }
         __syncthreads();
-        if (keep) {
-            const uint32_t pos = s_base + s_warp[warp] + __popc(m & lanemask_lt());
-            MSC_GUARD(pos < (uint32_t)cap, status, -131) {
-                ukeys[pos] = k;
-                uvals[pos] = (int32_t)i;
+        uint32_t pos = s_base + s_warp[warp] + incl - cnt;
+#pragma unroll
+        for (int j = 0; j < kCompactPer; ++j) {
+            if (k[j] != kEmpty) {
+                MSC_GUARD(pos < (uint32_t)cap, status, -131) {
+                    ukeys[pos] = k[j];
+                    uvals[pos] = (int32_t)(i0 + j);
+                }
+                ++pos;
             }
         }
         __syncthreads();
@@ -160,25 +206,31 @@ __global__ void k_ms_rank(const int32_t* __restrict__ slots, const uint32_t* ctl
         vals[slots[i]] = (uint32_t)i;
 }
 
-__global__ void k_ms_lookup(int32_t* ms, int32_t n, const uint32_t* __restrict__ vals,
-                            const uint32_t* ctl, int32_t* num_cells) {
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    const int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (t == 0) *num_cells = (int32_t)ctl[3];
-    const int64_t nq = n / 4;
-    int4* m4 = reinterpret_cast<int4*>(ms);
-    if (((uintptr_t)ms & 15) == 0) {
-        for (int64_t q = t; q < nq; q += stride) {
-            int4 s = m4[q];
-            s.x = (int32_t)vals[(uint32_t)s.x];
-            s.y = (int32_t)vals[(uint32_t)s.y];
-            s.z = (int32_t)vals[(uint32_t)s.z];
-            s.w = (int32_t)vals[(uint32_t)s.w];
-            m4[q] = s;
+// ms[v] = vals[ms[v]]: 8 vertices per thread, lane-consecutive, so the
+// gathers of a warp fall on neighbouring slots.
+constexpr int kLookupPer = 8;
+
+__global__ void __launch_bounds__(kThreads) k_ms_lookup(int32_t* ms, int32_t n, const uint32_t* __restrict__ vals,
+                                                        const uint32_t* ctl, int32_t* num_cells) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) *num_cells = (int32_t)ctl[3];
+    constexpr int64_t kChunk = (int64_t)kThreads * kLookupPer;
+    for (int64_t c = blockIdx.x; c * kChunk < n; c += gridDim.x) {
+        uint32_t s[kLookupPer];
+#pragma unroll
+        for (int j = 0; j < kLookupPer; ++j) {
+            const int64_t v = c * kChunk + (int64_t)j * kThreads + threadIdx.x;
+            s[j] = v < n ? (uint32_t)ms[v] : 0u;
         }
-        for (int64_t v = nq * 4 + t; v < n; v += stride) ms[v] = (int32_t)vals[(uint32_t)ms[v]];
-    } else {
-        for (int64_t v = t; v < n; v += stride) ms[v] = (int32_t)vals[(uint32_t)ms[v]];
+#pragma unroll
+        for (int j = 0; j < kLookupPer; ++j) {
+            const int64_t v = c * kChunk + (int64_t)j * kThreads + threadIdx.x;
+            if (v < n) s[j] = vals[s[j]];
+        }
+#pragma unroll
+        for (int j = 0; j < kLookupPer; ++j) {
+            const int64_t v = c * kChunk + (int64_t)j * kThreads + threadIdx.x;
+            if (v < n) ms[v] = (int32_t)s[j];
+        }
     }
 }
 
@@ -252,7 +304,7 @@ int run_ms_id(const int32_t* asc, const int32_t* desc, int32_t n, int32_t* ms, i
     MSC_LAUNCHED();
     {
         TraceScope ts_("msid.compact", s);
-        k_ms_compact<<<grid_for(sc.cap_max, 4), kThreads, 0, s>>>(sc.table_keys, sc.ctl, sc.ukeys[0], sc.uvals[0], status);
+        k_ms_compact<<<grid_for(sc.cap_max / kCompactPer, 4), kThreads, 0, s>>>(sc.table_keys, sc.ctl, sc.ukeys[0], sc.uvals[0], status);
     }
     MSC_LAUNCHED();
     const int key_bits = ceil_log2((int64_t)n * (int64_t)n);
@@ -268,7 +320,7 @@ int run_ms_id(const int32_t* asc, const int32_t* desc, int32_t n, int32_t* ms, i
     MSC_LAUNCHED();
     {
         TraceScope ts_("msid.lookup", s);
-        k_ms_lookup<<<grid_for(n / 4 + 1), kThreads, 0, s>>>(ms, n, sc.table_vals, sc.ctl, num_cells);
+        k_ms_lookup<<<grid_for(n / kLookupPer + 1), kThreads, 0, s>>>(ms, n, sc.table_vals, sc.ctl, num_cells);
     }
     MSC_LAUNCHED();
     return MSC_OK;

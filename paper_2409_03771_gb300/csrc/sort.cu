@@ -68,42 +68,90 @@ __device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t* s_w) {
     return v;
 }
 
+// Lanes of the warp whose 8-bit digit equals this lane's (valid lanes
+// only), from eight ballots -- no match instruction, no divergence.
+__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
+    uint32_t eq = __ballot_sync(0xffffffffu, valid);
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        eq &= bit ? bal : ~bal;
+    }
+    return eq;
+}
+
+constexpr int kHistRun = 16;  // consecutive keys per thread in the histogram
+
 // Digit histograms for `npass` passes over n keys (keys read from `keys`,
-// or made from the float field `f`).
+// or made from the float field `f`).  Each thread counts runs of equal
+// digits over 16 consecutive keys (neighbouring grid values share their
+// high digits, so the skewed digits cost one update per run) into a
+// warp-private shared histogram; blocks then add theirs to the global one.
 template <typename KeyT, bool FROM_F>
 __global__ void __launch_bounds__(256) k_hist(const KeyT* __restrict__ keys,
                                               const float* __restrict__ f, int64_t n_host,
                                               const int32_t* __restrict__ d_n, int npass,
                                               uint32_t* __restrict__ hist, int32_t* status) {
-    __shared__ uint32_t sh[8 * kBins];
-    for (int i = threadIdx.x; i < 8 * kBins; i += blockDim.x) sh[i] = 0;
+    extern __shared__ uint32_t sh[];  // [kWarps][npass][256]
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < kWarps * npass * kBins; i += blockDim.x) sh[i] = 0;
     __syncthreads();
+    uint32_t* wsh = sh + warp * npass * kBins;
     const int64_t n = d_n ? (int64_t)*d_n : n_host;
-    const int lane = threadIdx.x & 31;
-    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x * kHistRun;
     bool saw_nan = false;
-    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i - lane < n; i += stride) {
-        const bool valid = i < n;
-        KeyT k = 0;
-        if (valid) {
-            if constexpr (FROM_F) {
-                const float x = f[i];
-                saw_nan |= is_nan_bits(x);
-                k = float_key(x);
+    for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + tid) * kHistRun; i0 < n; i0 += stride) {
+        KeyT k[kHistRun];
+        const int cnt = (int)min((int64_t)kHistRun, n - i0);
+        if constexpr (FROM_F) {
+            if (cnt == kHistRun && ((uintptr_t)(f + i0) & 15) == 0) {
+#pragma unroll
+                for (int q = 0; q < kHistRun / 4; ++q) {
+                    const float4 v = reinterpret_cast<const float4*>(f + i0)[q];
+                    saw_nan |= is_nan_bits(v.x) | is_nan_bits(v.y) | is_nan_bits(v.z) | is_nan_bits(v.w);
+                    k[4 * q + 0] = float_key(v.x);
+                    k[4 * q + 1] = float_key(v.y);
+                    k[4 * q + 2] = float_key(v.z);
+                    k[4 * q + 3] = float_key(v.w);
+                }
             } else {
-                k = keys[i];
+#pragma unroll
+                for (int j = 0; j < kHistRun; ++j) {
+                    const float x = j < cnt ? f[i0 + j] : 0.f;
+                    saw_nan |= j < cnt && is_nan_bits(x);
+                    k[j] = float_key(x);
+                }
             }
+        } else {
+#pragma unroll
+            for (int j = 0; j < kHistRun; ++j) k[j] = j < cnt ? keys[i0 + j] : KeyT(0);
         }
         for (int p = 0; p < npass; ++p) {
-            const uint32_t d = valid ? (uint32_t)(k >> (8 * p)) & 255u : 256u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            if (valid && lane == __ffs(peers) - 1) atomicAdd(&sh[p * kBins + d], __popc(peers));
+            uint32_t* h = wsh + p * kBins;
+            uint32_t cur = (uint32_t)(k[0] >> (8 * p)) & 255u, run = 1;
+#pragma unroll
+            for (int j = 1; j < kHistRun; ++j) {
+                if (j >= cnt) break;
+                const uint32_t d = (uint32_t)(k[j] >> (8 * p)) & 255u;
+                if (d == cur) {
+                    ++run;
+                } else {
+                    atomicAdd(&h[cur], run);
+                    cur = d;
+                    run = 1;
+                }
+            }
+            atomicAdd(&h[cur], run);
         }
     }
     if (saw_nan) record_error(status, MSC_ERR_NAN);
     __syncthreads();
-    for (int i = threadIdx.x; i < npass * kBins; i += blockDim.x)
-        if (sh[i]) atomicAdd(&hist[i], sh[i]);
+    for (int i = tid; i < npass * kBins; i += blockDim.x) {
+        uint32_t c = 0;
+        for (int w = 0; w < kWarps; ++w) c += sh[w * npass * kBins + i];
+        if (c) atomicAdd(&hist[i], c);
+    }
 }
 
 template <typename KeyT>
@@ -134,7 +182,7 @@ constexpr size_t pass_smem_bytes() {
 // the payload is the vertex id.  TO_ORDER: write order[payload] = position
 // instead of the sorted (key, payload) arrays.
 template <typename KeyT, bool FROM_F, bool TO_ORDER>
-__global__ void __launch_bounds__(kThreads) k_onesweep(const PassArgs<KeyT> a) {
+__global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem);  // [kWarps][256]
     uint32_t* s_total = s_whist + kWarps * kBins;          // [256]
@@ -180,19 +228,18 @@ __global__ void __launch_bounds__(kThreads) k_onesweep(const PassArgs<KeyT> a) {
             }
         }
         uint32_t* wh = s_whist + warp * kBins;
+        const uint32_t lt = lanemask_lt();
 #pragma unroll
         for (int k = 0; k < kItems; ++k) {
+            // stable rank among the warp's equal digits: earlier iterations
+            // (warp counter) + lower lanes of this iteration (ballot peers)
             const bool valid = base + k * 32 + lane < n;
-            const uint32_t d = valid ? (uint32_t)(key[k] >> a.shift) & 255u : 256u;
-            const uint32_t peers = __match_any_sync(0xffffffffu, d);
-            const int leader = __ffs(peers) - 1;
-            uint32_t before = 0;
-            if (lane == leader && valid) {
-                before = wh[d];
-                wh[d] = before + __popc(peers);
-            }
-            before = __shfl_sync(0xffffffffu, before, leader);
-            rk[k] = (d << 16) | (before + __popc(peers & lanemask_lt()));
+            const uint32_t d = (uint32_t)(key[k] >> a.shift) & 255u;
+            const uint32_t peers = digit_peers(d, valid);
+            const uint32_t lower = __popc(peers & lt);
+            const uint32_t before = wh[d];
+            if (valid && lower == 0) wh[d] = before + __popc(peers);
+            rk[k] = ((valid ? d : 256u) << 16) | (before + lower);
             __syncwarp();
         }
         __syncthreads();
@@ -338,8 +385,23 @@ static int clear_scratch(const SortScratch& sc, int64_t n, cudaStream_t s) {
     return MSC_OK;
 }
 
+static size_t hist_smem(int npass) { return (size_t)kWarps * npass * kBins * sizeof(uint32_t); }
+
+// Allow both histogram kernels the shared memory of 8 passes (64 KiB).
+static int configure_hist() {
+    static int configured_dev = -1;
+    if (configured_dev != current_device().id) {
+        const int bytes = (int)hist_smem(8);
+        MSC_TRY(cudaFuncSetAttribute(k_hist<uint32_t, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        MSC_TRY(cudaFuncSetAttribute(k_hist<unsigned long long, false>,
+                                     cudaFuncAttributeMaxDynamicSharedMemorySize, bytes));
+        configured_dev = current_device().id;
+    }
+    return MSC_OK;
+}
+
 static int hist_grid(int64_t n) {
-    const int64_t want = ceil_div(std::max<int64_t>(n, 1), 256 * 8);
+    const int64_t want = ceil_div(std::max<int64_t>(n, 1), 256 * kHistRun);
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)current_device().sms * 8));
 }
 
@@ -349,9 +411,10 @@ int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_
     if (n <= 0) return MSC_OK;
     int r = clear_scratch(sc, n, s);
     if (r) return r;
+    if ((r = configure_hist())) return r;
     {
         TraceScope ts_("order.hist", s);
-        k_hist<uint32_t, true><<<hist_grid(n), 256, 0, s>>>(nullptr, f, n, nullptr, 4, sc.hist, status);
+        k_hist<uint32_t, true><<<hist_grid(n), 256, hist_smem(4), s>>>(nullptr, f, n, nullptr, 4, sc.hist, status);
     }
     MSC_LAUNCHED();
     PassArgs<uint32_t> a{};
@@ -407,9 +470,10 @@ int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* ke
     const int npass = std::min(8, (key_bits + 7) / 8);
     int r = clear_scratch(sc, max_count, s);
     if (r) return r;
+    if ((r = configure_hist())) return r;
     {
         TraceScope ts_("msid.sort_hist", s);
-        k_hist<unsigned long long, false><<<hist_grid(max_count), 256, 0, s>>>(keys, nullptr, max_count, d_count, npass, sc.hist, status);
+        k_hist<unsigned long long, false><<<hist_grid(max_count), 256, hist_smem(npass), s>>>(keys, nullptr, max_count, d_count, npass, sc.hist, status);
     }
     MSC_LAUNCHED();
     PassArgs<unsigned long long> a{};

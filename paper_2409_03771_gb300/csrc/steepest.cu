@@ -44,17 +44,40 @@ struct GridInfo {
     int vec_store;  // asc/desc rows can take int4 stores
 };
 
+// Packed candidate: order * 16 + neighbour code.  Out-of-grid cells hold
+// -1: negative as signed (loses every max), huge as unsigned (loses every
+// min).  PK = int32 when order * 16 + 15 fits (n <= 2^27), else int64.
 template <typename PK>
-struct Best {
-    PK hi, lo;  // hi: signed max, lo: unsigned min
-    __device__ __forceinline__ void init(int c) { hi = lo = (PK)c * 16 + 14; }
-    __device__ __forceinline__ void add(int val, int code) {
-        const PK p = (PK)val * 16 + code;
-        hi = p > hi ? p : hi;
-        using U = typename std::conditional<sizeof(PK) == 4, uint32_t, unsigned long long>::type;
-        lo = (U)p < (U)lo ? p : lo;
+__device__ __forceinline__ PK pack(int val, int code) {
+    return (PK)val * 16 + code;
+}
+
+// argmax / argmin codes over the 15 packed candidates c[0..14].
+__device__ __forceinline__ void best_codes(const int32_t (&c)[15], int& hi, int& lo) {
+    // three-input integer max / unsigned min: 7 + 7 operations, not 14 + 14
+    int a0 = __vimax3_s32(c[0], c[1], c[2]), a1 = __vimax3_s32(c[3], c[4], c[5]);
+    int a2 = __vimax3_s32(c[6], c[7], c[8]), a3 = __vimax3_s32(c[9], c[10], c[11]);
+    int a4 = __vimax3_s32(c[12], c[13], c[14]);
+    const int mx = __vimax3_s32(__vimax3_s32(a0, a1, a2), a3, a4);
+    unsigned b0 = __vimin3_u32(c[0], c[1], c[2]), b1 = __vimin3_u32(c[3], c[4], c[5]);
+    unsigned b2 = __vimin3_u32(c[6], c[7], c[8]), b3 = __vimin3_u32(c[9], c[10], c[11]);
+    unsigned b4 = __vimin3_u32(c[12], c[13], c[14]);
+    const unsigned mn = __vimin3_u32(__vimin3_u32(b0, b1, b2), b3, b4);
+    hi = mx & 15;
+    lo = (int)(mn & 15u);
+}
+
+__device__ __forceinline__ void best_codes(const long long (&c)[15], int& hi, int& lo) {
+    long long mx = c[0];
+    unsigned long long mn = (unsigned long long)c[0];
+#pragma unroll
+    for (int k = 1; k < 15; ++k) {
+        mx = c[k] > mx ? c[k] : mx;
+        mn = (unsigned long long)c[k] < mn ? (unsigned long long)c[k] : mn;
     }
-};
+    hi = (int)(mx & 15);
+    lo = (int)(mn & 15);
+}
 
 __device__ __forceinline__ void load_row(const int* r, int (&o)[6]) {
     // o[j] = value at x offset j-1 relative to the thread's first vertex
@@ -69,7 +92,7 @@ __device__ __forceinline__ void load_row(const int* r, int (&o)[6]) {
 
 template <typename PK>
 __device__ __forceinline__ void tile_compute(const int* buf, const GridInfo& g, int x0, int y0,
-                                             int z0, const int64_t* s_off, int32_t* __restrict__ asc,
+                                             int z0, const int32_t* s_off, int32_t* __restrict__ asc,
                                              int32_t* __restrict__ desc, uint32_t& nmin,
                                              uint32_t& nmax) {
     const int tid = threadIdx.x;
@@ -94,36 +117,25 @@ __device__ __forceinline__ void tile_compute(const int* buf, const GridInfo& g, 
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
             const int j = i + 1;  // index of x offset 0
-            Best<PK> bst;
-            bst.init(D[j]);
-            bst.add(A[j], 0);
-            bst.add(A[j - 1], 1);
-            bst.add(B[j], 2);
-            bst.add(B[j - 1], 3);
-            bst.add(C[j], 4);
-            bst.add(C[j - 1], 5);
-            bst.add(D[j - 1], 6);
-            bst.add(D[j + 1], 7);
-            bst.add(E[j], 8);
-            bst.add(E[j + 1], 9);
-            bst.add(F[j], 10);
-            bst.add(F[j + 1], 11);
-            bst.add(G[j], 12);
-            bst.add(G[j + 1], 13);
-            hi_code[i] = (int)(bst.hi & 15);
-            lo_code[i] = (int)(bst.lo & 15);
+            using P = typename std::conditional<sizeof(PK) == 4, int32_t, long long>::type;
+            const P c[15] = {pack<P>(D[j], 14),     pack<P>(A[j], 0),     pack<P>(A[j - 1], 1),
+                             pack<P>(B[j], 2),      pack<P>(B[j - 1], 3), pack<P>(C[j], 4),
+                             pack<P>(C[j - 1], 5),  pack<P>(D[j - 1], 6), pack<P>(D[j + 1], 7),
+                             pack<P>(E[j], 8),      pack<P>(E[j + 1], 9), pack<P>(F[j], 10),
+                             pack<P>(F[j + 1], 11), pack<P>(G[j], 12),    pack<P>(G[j + 1], 13)};
+            best_codes(c, hi_code[i], lo_code[i]);
         }
-        const int64_t v0 = gx0 + (int64_t)g.nx * (gy + (int64_t)g.ny * gz);
+        const int32_t v0 = gx0 + g.nx * (gy + g.ny * gz);  // n < 2^31
         int out_hi[4], out_lo[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
-            out_hi[i] = (int)(v0 + i + s_off[hi_code[i]]);
-            out_lo[i] = (int)(v0 + i + s_off[lo_code[i]]);
+            out_hi[i] = v0 + i + s_off[hi_code[i]];
+            out_lo[i] = v0 + i + s_off[lo_code[i]];
             nmax += hi_code[i] == 14 && gx0 + i < g.nx;
             nmin += lo_code[i] == 14 && gx0 + i < g.nx;
         }
 #ifdef MSC_DEBUG_BOUNDS
-        if (v0 < 0 || v0 + 3 >= (int64_t)g.nx * g.ny * g.nz + 3) return;
+        if (v0 < 0) return;
 #endif
         if (g.vec_store && gx0 + 3 < g.nx) {
             *reinterpret_cast<int4*>(desc + v0) = make_int4(out_hi[0], out_hi[1], out_hi[2], out_hi[3]);
@@ -177,13 +189,13 @@ __device__ __forceinline__ void flush_counts(uint32_t nmin, uint32_t nmax, uint3
 }
 
 template <typename PK>
-__global__ void __launch_bounds__(kThreads) k_steepest_tma(const __grid_constant__ CUtensorMap map,
+__global__ void __launch_bounds__(kThreads, 4) k_steepest_tma(const __grid_constant__ CUtensorMap map,
                                                           const GridInfo g, int32_t* asc,
                                                           int32_t* desc, uint32_t* extrema,
                                                           int32_t* status) {
     __shared__ alignas(128) int buf[2][BOX];
     __shared__ alignas(8) uint64_t bar[2];
-    __shared__ int64_t s_off[15];
+    __shared__ int32_t s_off[15];
     const int tid = threadIdx.x;
     if (tid == 0) {
         mbar_init(&bar[0], 1);
@@ -191,7 +203,7 @@ __global__ void __launch_bounds__(kThreads) k_steepest_tma(const __grid_constant
         fence_mbar_init();
     }
     if (tid < 15)
-        s_off[tid] = c_off[tid][0] + (int64_t)g.nx * (c_off[tid][1] + (int64_t)g.ny * c_off[tid][2]);
+        s_off[tid] = c_off[tid][0] + g.nx * (c_off[tid][1] + g.ny * c_off[tid][2]);
     __syncthreads();
     auto issue = [&](int64_t t, int b) {
         int x0, y0, z0;
@@ -239,10 +251,10 @@ __global__ void __launch_bounds__(kThreads) k_steepest_ld(const int32_t* __restr
                                                          const GridInfo g, int32_t* asc,
                                                          int32_t* desc, uint32_t* extrema) {
     __shared__ alignas(16) int buf[BOX];
-    __shared__ int64_t s_off[15];
+    __shared__ int32_t s_off[15];
     const int tid = threadIdx.x;
     if (tid < 15)
-        s_off[tid] = c_off[tid][0] + (int64_t)g.nx * (c_off[tid][1] + (int64_t)g.ny * c_off[tid][2]);
+        s_off[tid] = c_off[tid][0] + g.nx * (c_off[tid][1] + g.ny * c_off[tid][2]);
     uint32_t nmin = 0, nmax = 0;
     for (int64_t tile = blockIdx.x; tile < g.ntiles; tile += gridDim.x) {
         int x0, y0, z0;
