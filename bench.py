@@ -199,6 +199,7 @@ def run_ours(args):
     mlab = torch.empty(nm, **i32)
     ws = torch.empty(msc.msc_workspace_bytes(msc.OP_SEGMENT, n), dtype=torch.uint8, device=dev)
     small_ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    mesh_ws = torch.empty(msc.msc_workspace_bytes(msc.OP_CC_MESH, nm, nnz), dtype=torch.uint8, device=dev)
     status = torch.zeros(4, **i32)
     stream = torch.cuda.current_stream(dev)
 
@@ -210,7 +211,7 @@ def run_ours(args):
             assert r == 0, msc.msc_status_string(r)
         r = msc.msc_cc_mask(mk, dims, 6, lab, small_ws, small_ws.numel(), status[2:3], stream)
         assert r == 0, msc.msc_status_string(r)
-        r = msc.msc_cc_mesh(rw, cl, nm, mlab, small_ws, small_ws.numel(), status[3:4], stream)
+        r = msc.msc_cc_mesh(rw, cl, nm, mlab, mesh_ws, mesh_ws.numel(), status[3:4], stream)
         assert r == 0, msc.msc_status_string(r)
 
     def check_status(where):

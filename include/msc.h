@@ -183,7 +183,13 @@ MSC_API int msc_cc_mask(const uint8_t* mask, msc_grid g, int32_t conn, int32_t* 
  *   row, col  device int32 CSR (row[n+1], col[row[n]]), symmetric.
  *   label     device int32[n] out: smallest vertex id of the component; a
  *             vertex with no edge labels itself.
- * A column outside [0, n) sets MSC_ERR_ARG in d_status. */
+ * Workspace: msc_workspace_bytes(MSC_OP_CC_MESH, n, nnz).  A column
+ * outside [0, n) sets MSC_ERR_ARG in d_status.
+ * Method: union-find with min-label hooking and subgraph sampling: every
+ * vertex is first united with two of its neighbours, the most frequent
+ * label of a sample names the dominant component, only vertices outside it
+ * unite their remaining edges, and pointer jumping labels every vertex
+ * with its root. */
 MSC_API int msc_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* label, void* ws,
                 size_t ws_bytes, int32_t* d_status, void* stream);
 

@@ -8,18 +8,19 @@
 // tiles, mirrored to the smallest id, with the hooking made exact by a
 // union-find on roots (hook the larger root under the smaller with
 // atomicMin; retry if another thread moved it first):
-//   1. k_cc_local: a 64x8x8 tile of the mask in shared memory, union-find
-//      over its internal edges in shared memory, each feature voxel
-//      written with the global id of its tile-local root (the smallest id
-//      of its tile-local component), -1 elsewhere;
+//   1. k_cc_local: a 64x8x8 tile of the mask as 64 row bitmasks in shared
+//      memory, x-runs labelled by bit arithmetic, runs of neighbouring rows
+//      united once per overlap segment, each feature voxel written with
+//      the global id of its tile-local root (the smallest id of its
+//      tile-local component), -1 elsewhere;
 //   2. k_cc_merge: for every edge that leaves a tile through its +x, +y or
 //      +z side, union the two roots in global memory (path halving);
 //   3. k_cc_flatten: pointer jumping to the final root.
 // The final root of a component is its smallest vertex id because every
 // hook points a root at a smaller one.
 //
-// Mesh: label[v] <- min(v, smallest neighbour), union over every edge
-// (u < v) in global memory, flatten.
+// Mesh: union-find over the CSR edges with subgraph sampling (see the mesh
+// kernels below).
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -118,44 +119,91 @@ __device__ __forceinline__ void union_g(int32_t* L, int32_t a, int32_t b, int32_
     record_error(status, MSC_ERR_INTERNAL);
 }
 
+// Tile-local labelling, run based.  Rows are x-lines of 64 voxels (one
+// 64-bit mask each, from two ballots).  A masked voxel starts at the first
+// voxel of its x-run; runs of neighbouring rows are united once per
+// overlap segment (a maximal x-range where both rows' voxels, shifted by
+// the offset's dx, are masked); then every voxel takes its root.
+constexpr int kRows = CY * CZ;  // 64 rows of CX = 64 voxels
+
+__device__ __forceinline__ uint64_t run_start_mask_below(uint64_t m, int x) {
+    return ~m & ((x ? (~0ull >> (64 - x)) : 0ull));
+}
+
 __global__ void __launch_bounds__(kThreads) k_cc_local(const uint8_t* __restrict__ mask, const CcGrid g,
                                                        int32_t* __restrict__ label) {
     __shared__ int s_l[CT];
-    __shared__ uint8_t s_m[CT];
-    const int tid = threadIdx.x;
-    const int npos = g.conn == 6 ? 3 : 7;
+    __shared__ uint64_t s_row[kRows];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         int x0, y0, z0;
         cc_tile_coords(g, t, x0, y0, z0);
+        // rows: warp w takes rows w, w + 8, ..., 8 rows per warp
+        for (int r = warp; r < kRows; r += kThreads / 32) {
+            const int ly = r & (CY - 1), lz = r / CY;
+            const int gy = y0 + ly, gz = z0 + lz;
+            bool a = false, b = false;
+            if (gy < g.ny && gz < g.nz) {
+                const int64_t rb = (int64_t)g.nx * (gy + (int64_t)g.ny * gz);
+                if (x0 + lane < g.nx) a = mask[rb + x0 + lane] != 0;
+                if (x0 + 32 + lane < g.nx) b = mask[rb + x0 + 32 + lane] != 0;
+            }
+            const uint64_t m = (uint64_t)__ballot_sync(0xffffffffu, a) | ((uint64_t)__ballot_sync(0xffffffffu, b) << 32);
+            if (lane == 0) s_row[r] = m;
 #pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int i = tid + k * kThreads;
-            const int lx = i & (CX - 1), ly = (i / CX) & (CY - 1), lz = i / (CX * CY);
-            const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-            uint8_t m = 0;
-            if (gx < g.nx && gy < g.ny && gz < g.nz)
-                m = mask[gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz)] != 0;
-            s_m[i] = m;
-            s_l[i] = m ? i : -1;
+            for (int h = 0; h < 2; ++h) {
+                const int x = lane + 32 * h;
+                int lab = -1;
+                if (m >> x & 1ull) {
+                    const uint64_t z = run_start_mask_below(m, x);
+                    const int start = z ? 64 - __clzll((long long)z) : 0;
+                    lab = start + CX * r;
+                }
+                s_l[x + CX * r] = lab;
+            }
         }
         __syncthreads();
-#pragma unroll 1
-        for (int k = 0; k < kPer; ++k) {
-            const int i = tid + k * kThreads;
-            if (!s_m[i]) continue;
-            const int lx = i & (CX - 1), ly = (i / CX) & (CY - 1), lz = i / (CX * CY);
-            for (int o = 0; o < npos; ++o) {
-                const int jx = lx + c_pos[o][0], jy = ly + c_pos[o][1], jz = lz + c_pos[o][2];
-                if (jx >= CX || jy >= CY || jz >= CZ) continue;
-                const int j = jx + CX * (jy + CY * jz);
-                if (s_m[j]) union_s(s_l, i, j);
+        // unite runs of neighbouring rows, once per overlap segment
+        const int npairs = g.conn == 6 ? 2 * 56 : 2 * 56 + 2 * 56 + 2 * 49;
+        for (int q = tid; q < npairs; q += kThreads) {
+            int r, r2, dx;
+            int k = q;
+            if (k < 112) {  // (0,1,0) / (1,1,0): y + 1 ; (0,0,1) / (1,0,1): z + 1
+                const bool ystep = k < 56;
+                const int i = ystep ? k : k - 56;
+                const int ly = ystep ? i % 7 : i % 8, lz = ystep ? i / 7 : i / 8;
+                r = ly + CY * lz;
+                r2 = ystep ? r + 1 : r + CY;
+                dx = 0;
+            } else if (k < 224) {
+                k -= 112;
+                const bool ystep = k < 56;
+                const int i = ystep ? k : k - 56;
+                const int ly = ystep ? i % 7 : i % 8, lz = ystep ? i / 7 : i / 8;
+                r = ly + CY * lz;
+                r2 = ystep ? r + 1 : r + CY;
+                dx = 1;
+            } else {  // (0,1,1) / (1,1,1): y + 1 and z + 1
+                k -= 224;
+                const int i = k % 49;
+                const int ly = i % 7, lz = i / 7;
+                r = ly + CY * lz;
+                r2 = r + 1 + CY;
+                dx = k < 49 ? 0 : 1;
+            }
+            const uint64_t o = s_row[r] & (s_row[r2] >> dx);
+            uint64_t seg = o & ~(o << 1);
+            while (seg) {
+                const int x = __ffsll((long long)seg) - 1;
+                seg &= seg - 1;
+                union_s(s_l, s_l[x + CX * r], s_l[x + dx + CX * r2]);
             }
         }
         __syncthreads();
 #pragma unroll
         for (int k = 0; k < kPer; ++k) {
             const int i = tid + k * kThreads;
-            if (s_m[i]) s_l[i] = find_s(s_l, i);
+            if (s_l[i] >= 0) s_l[i] = find_s(s_l, i);
         }
         __syncthreads();
 #pragma unroll
@@ -270,62 +318,102 @@ __global__ void __launch_bounds__(kFlatThreads) k_flatten(int32_t* label, int64_
 // ----------------------------------------------------------------------------
 // mesh
 
-// Mesh kernels: 8 lanes per vertex, each lane taking every 8th entry of
-// the row, so a row's column indices are read as contiguous 32-byte runs.
+// Mesh kernels (subgraph sampling, after the Afforest scheme):
+//   1. label[v] = v; unite every vertex with its first and second neighbour
+//      (one lane per vertex and round);
+//   2. flatten; sample 1024 vertices and take the most frequent label --
+//      on a well-connected mesh, nearly every vertex is already in that
+//      component;
+//   3. every vertex outside it unites all its remaining edges (8 lanes per
+//      row); an edge to a vertex of the frequent component is found from
+//      this side, since the adjacency is symmetric;
+//   4. flatten.
+// Every union hooks the larger root under the smaller, so the final root of
+// a component is its smallest vertex id, whatever the order of unions.
 constexpr int kRowLanes = 8;
+constexpr int kSamples = 1024;
 
-__global__ void __launch_bounds__(256) k_mesh_init(const int32_t* __restrict__ row,
-                                                   const int32_t* __restrict__ col, int32_t n,
-                                                   int32_t* label, int32_t* status) {
-    const int sub = threadIdx.x & (kRowLanes - 1);
-    const int64_t warps = ((int64_t)gridDim.x * blockDim.x) / 32;
-    constexpr int kPerWarp = 32 / kRowLanes;
-    for (int64_t wbase = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32) * kPerWarp; wbase < n;
-         wbase += warps * kPerWarp) {
-        const int64_t v = wbase + (threadIdx.x & 31) / kRowLanes;
-        int32_t m = INT32_MAX;
-        if (v < n) {
-            m = (int32_t)v;
-            const int32_t e1 = row[v + 1];
-            for (int32_t e = row[v] + sub; e < e1; e += kRowLanes) {
-                const int32_t u = col[e];
-                if ((uint32_t)u >= (uint32_t)n) {
-                    record_error(status, MSC_ERR_ARG);
-                    continue;
-                }
-                m = u < m ? u : m;
-            }
+__global__ void k_mesh_init(int32_t* label, int32_t n) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x)
+        label[v] = (int32_t)v;
+}
+
+// Unite every vertex with its k-th neighbour (k = 0 or 1).
+__global__ void k_mesh_link_k(const int32_t* __restrict__ row, const int32_t* __restrict__ col, int32_t n,
+                              int k, int32_t* label, int32_t* status) {
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t e = row[v] + k;
+        if (e >= row[v + 1]) continue;
+        const int32_t u = col[e];
+        if ((uint32_t)u >= (uint32_t)n) {
+            record_error(status, MSC_ERR_ARG);
+            continue;
         }
-#pragma unroll
-        for (int o = kRowLanes / 2; o > 0; o >>= 1) {
-            const int32_t t = __shfl_xor_sync(0xffffffffu, m, o);
-            m = t < m ? t : m;
-        }
-        if (v < n && sub == 0) label[v] = m;
+        union_g(label, (int32_t)v, u, status);
     }
 }
 
-// Union every edge (v, u) with u < v, after label[] holds, for every v, the
-// smallest of v and its neighbours.  The root of v is found once per row.
+// The most frequent label among kSamples vertices spread over the ids
+// (one block; labels sorted in shared memory, longest run wins, ties to
+// the smaller label).
+__global__ void __launch_bounds__(kSamples) k_mesh_sample(const int32_t* label, int32_t n, int32_t* frequent) {
+    __shared__ int32_t s[kSamples];
+    __shared__ int32_t s_best[2];  // label, run length
+    const int t = threadIdx.x;
+    const uint64_t mixed = (uint64_t)(t + 1) * 0x9e3779b97f4a7c15ull;
+    s[t] = label[(int64_t)((mixed >> 11) % (uint64_t)n)];
+    __syncthreads();
+    for (int k = 2; k <= kSamples; k <<= 1)  // bitonic sort
+        for (int j = k >> 1; j > 0; j >>= 1) {
+            const int p = t ^ j;
+            if (p > t) {
+                const bool up = (t & k) == 0;
+                const int32_t a = s[t], b = s[p];
+                if ((a > b) == up) {
+                    s[t] = b;
+                    s[p] = a;
+                }
+            }
+            __syncthreads();
+        }
+    if (t == 0) {
+        int32_t best = s[0], best_len = 0, cur = s[0], len = 0;
+        for (int i = 0; i < kSamples; ++i) {
+            if (s[i] == cur) ++len;
+            else {
+                cur = s[i];
+                len = 1;
+            }
+            if (len > best_len) {
+                best_len = len;
+                best = cur;
+            }
+        }
+        *frequent = best;
+    }
+}
+
+// Vertices outside the frequent component unite their remaining edges.
 __global__ void __launch_bounds__(256) k_mesh_hook(const int32_t* __restrict__ row,
                                                    const int32_t* __restrict__ col, int32_t n,
-                                                   int32_t* label, int32_t* status) {
+                                                   const int32_t* __restrict__ frequent, int32_t* label,
+                                                   int32_t* status) {
     const int lane = threadIdx.x & 31, sub = lane & (kRowLanes - 1);
+    const int32_t big = *frequent;
     const int64_t warps = ((int64_t)gridDim.x * blockDim.x) / 32;
     constexpr int kPerWarp = 32 / kRowLanes;
     for (int64_t wbase = (((int64_t)blockIdx.x * blockDim.x + threadIdx.x) / 32) * kPerWarp; wbase < n;
          wbase += warps * kPerWarp) {
         const int64_t v = wbase + lane / kRowLanes;
-        int32_t rv = 0;
-        if (v < n && sub == 0) rv = find_g(label, (int32_t)v);
-        rv = __shfl_sync(0xffffffffu, rv, lane & ~(kRowLanes - 1));
-        if (v >= n) continue;
+        if (v >= n || label[v] == big) continue;
         const int32_t e1 = row[v + 1];
-        for (int32_t e = row[v] + sub; e < e1; e += kRowLanes) {
+        for (int32_t e = row[v] + 2 + sub; e < e1; e += kRowLanes) {
             const int32_t u = col[e];
-            if ((uint32_t)u >= (uint32_t)v) continue;  // each edge once (u < v); bad u skipped
-            if (ld_volatile_s32(label + u) == rv) continue;  // already hooked to v's root
-            union_g(label, rv, u, status);
+            if ((uint32_t)u >= (uint32_t)n) {
+                record_error(status, MSC_ERR_ARG);
+                continue;
+            }
+            union_g(label, (int32_t)v, u, status);
         }
     }
 }
@@ -371,22 +459,38 @@ int run_cc_mask(const uint8_t* mask, msc_grid gd, int conn, int32_t* label, int3
 }
 
 int run_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* label, int32_t* status,
-                cudaStream_t s) {
+                cudaStream_t s, int32_t* frequent) {
     if (n <= 0) return MSC_OK;
     const int grid = cc_grid_for(n);
+    const int fgrid = cc_grid_for(ceil_div(n, kFlatPer));
     {
         TraceScope ts_("mesh.init", s);
-        k_mesh_init<<<grid, 256, 0, s>>>(row, col, n, label, status);
+        k_mesh_init<<<grid, 256, 0, s>>>(label, n);
     }
     MSC_LAUNCHED();
-    {
-        TraceScope ts_("mesh.hook", s);
-        k_mesh_hook<<<grid, 256, 0, s>>>(row, col, n, label, status);
+    for (int k = 0; k < 2; ++k) {
+        TraceScope ts_("mesh.link", s);
+        k_mesh_link_k<<<grid, 256, 0, s>>>(row, col, n, k, label, status);
     }
     MSC_LAUNCHED();
     {
         TraceScope ts_("mesh.flatten", s);
-        k_flatten<<<cc_grid_for(ceil_div(n, kFlatPer)), kFlatThreads, 0, s>>>(label, n);
+        k_flatten<<<fgrid, kFlatThreads, 0, s>>>(label, n);
+    }
+    MSC_LAUNCHED();
+    {
+        TraceScope ts_("mesh.sample", s);
+        k_mesh_sample<<<1, kSamples, 0, s>>>(label, n, frequent);
+    }
+    MSC_LAUNCHED();
+    {
+        TraceScope ts_("mesh.hook", s);
+        k_mesh_hook<<<grid, 256, 0, s>>>(row, col, n, frequent, label, status);
+    }
+    MSC_LAUNCHED();
+    {
+        TraceScope ts_("mesh.flatten", s);
+        k_flatten<<<fgrid, kFlatThreads, 0, s>>>(label, n);
     }
     MSC_LAUNCHED();
     return MSC_OK;

@@ -11,7 +11,8 @@ int run_cc_mask(const uint8_t* mask, msc_grid g, int conn, int32_t* label, int32
                 cudaStream_t s);
 
 // label[v] = smallest id of v's component of the symmetric CSR graph.
+// `frequent` is one device int32 of scratch.
 int run_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* label, int32_t* status,
-                cudaStream_t s);
+                cudaStream_t s, int32_t* frequent);
 
 }  // namespace msc

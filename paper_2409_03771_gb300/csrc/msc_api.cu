@@ -134,7 +134,7 @@ size_t msc_workspace_bytes(int op, int64_t n, int64_t nnz) {
             size_ms_scratch(s, n);
             return s.used;
         case MSC_OP_SEGMENT: return segment_bytes(n);
-        case MSC_OP_CC_MASK:
+        case MSC_OP_CC_MASK: return 256;
         case MSC_OP_CC_MESH: return 256;
         default: return 0;
     }
@@ -249,12 +249,12 @@ int msc_cc_mask(const uint8_t* mask, msc_grid g, int32_t conn, int32_t* label, v
 
 int msc_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* label, void* ws, size_t ws_bytes,
                 int32_t* d_status, void* stream) {
-    (void)ws;
-    if (n < 0 || !d_status || (n > 0 && (!row || !col || !label))) return MSC_ERR_ARG;
+    if (n < 0 || !d_status || (n > 0 && (!row || !col || !label || !ws))) return MSC_ERR_ARG;
     if (ws_bytes < msc_workspace_bytes(MSC_OP_CC_MESH, n, 0)) return MSC_ERR_WS;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
-    return run_cc_mesh(row, col, n, label, d_status, s);
+    if (n == 0) return MSC_OK;
+    return run_cc_mesh(row, col, n, label, d_status, s, static_cast<int32_t*>(ws));
 }
 
 }  // extern "C"
