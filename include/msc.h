@@ -193,6 +193,71 @@ MSC_API int msc_cc_mask(const uint8_t* mask, msc_grid g, int32_t conn, int32_t* 
 MSC_API int msc_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* label, void* ws,
                 size_t ws_bytes, int32_t* d_status, void* stream);
 
+/* ---------------------------------------------------------------------
+ * Batched segmentation.  The paper segments one grid at a time; a batch
+ * applies the computation of msc_segment (Alg. 1 for both manifolds, then
+ * the cell ids of section "Ascending and Descending Segmentation") to
+ * `count` independent grids in one pass over a packed vertex space.
+ * Grid i occupies ids [off_i, off_i + n_i) of every packed array, where
+ * n_i = nx*ny*nz, off_0 = 0 and off_{i+1} = off_i + n_i; the total
+ * sum n_i must stay below 2^31.  Every output is local to its instance and
+ * is byte for byte what msc_segment returns for that grid alone:
+ *   grids      host msc_grid[count] (read during the call only)
+ *   f          device float32[total]
+ *   order      device int32[total] out: rank of the vertex in its instance
+ *   asc, desc  device int32[total] out: instance-local id of the vertex's
+ *              minimum / maximum
+ *   ms         device int32[total] out: instance-local dense cell id
+ *   num_cells  device int32[count] out: cells of each instance
+ * Workspace: msc_batch_workspace_bytes(grids, count).  Device errors go to
+ * d_status as for msc_segment; a bad grid returns MSC_ERR_ARG. */
+
+/* Tuning knobs of the batched path.  None changes any output. */
+typedef struct {
+    int32_t steepest_shape; /* stencil tile: 0 = 32x8x8, 1 = 16x8x16, 2 = 64x4x8,
+                               3 = 16x16x8; -1 = tuned (msc_batch_autotune) or 0 */
+    int32_t build_shift;    /* pointer jumping switches to an active list once at
+                               most n >> build_shift pointers moved in a sweep
+                               (1..30); 0 = tuned or 3 */
+} msc_tune;
+
+MSC_API size_t msc_batch_workspace_bytes(const msc_grid* grids, int32_t count);
+
+/* One batched segmentation, enqueued as plain launches on `stream`.  The
+ * instance tables are copied from host memory at the start of the call.
+ * tune = NULL means { -1, 0 }. */
+MSC_API int msc_batch_segment(const msc_grid* grids, int32_t count, const float* f, int32_t* order,
+                              int32_t* asc, int32_t* desc, int32_t* ms, int32_t* num_cells, void* ws,
+                              size_t ws_bytes, const msc_tune* tune, int32_t* d_status, void* stream);
+
+/* The same batch captured once as a CUDA graph bound to these buffers.
+ * Each msc_batch_plan_launch replays the whole batch (status reset
+ * included) with one graph launch on `stream`; the inputs in f may change
+ * between launches, the grids and buffers may not.  Creating the plan
+ * copies the instance tables on `stream`, waits for that copy, and
+ * captures on a private stream (it launches no kernel).  msc_batch_plan_kernels gives the kernels one
+ * replay runs.  Destroy the plan before freeing its buffers. */
+typedef struct msc_batch_plan msc_batch_plan;
+MSC_API int msc_batch_plan_create(const msc_grid* grids, int32_t count, const float* f, int32_t* order,
+                                  int32_t* asc, int32_t* desc, int32_t* ms, int32_t* num_cells,
+                                  void* ws, size_t ws_bytes, const msc_tune* tune, int32_t* d_status,
+                                  void* stream, msc_batch_plan** plan);
+MSC_API int msc_batch_plan_launch(msc_batch_plan* plan, void* stream);
+MSC_API int msc_batch_plan_kernels(const msc_batch_plan* plan);
+MSC_API void msc_batch_plan_destroy(msc_batch_plan* plan);
+
+/* Autotuner: times the batch under candidate tunings (tile shapes first,
+ * then active-list thresholds for the best shape), `reps` timed runs each
+ * after one warm-up, and checks that every candidate produces the same
+ * outputs (a device checksum; a mismatch returns MSC_ERR_INTERNAL).  The
+ * winner goes to *best (and its mean time in ms to *best_ms) and is
+ * remembered for this list of grids: later calls with tune = NULL or
+ * auto fields use it.  Synchronises `stream`. */
+MSC_API int msc_batch_autotune(const msc_grid* grids, int32_t count, const float* f, int32_t* order,
+                               int32_t* asc, int32_t* desc, int32_t* ms, int32_t* num_cells, void* ws,
+                               size_t ws_bytes, int32_t* d_status, void* stream, int32_t reps,
+                               msc_tune* best, float* best_ms);
+
 #ifdef __cplusplus
 }
 #endif

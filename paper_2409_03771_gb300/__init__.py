@@ -31,6 +31,8 @@ __all__ = [
     "order", "steepest_grid", "steepest_csr", "compress", "ms_id", "segment", "cc_mask", "cc_mesh",
     "OP_ORDER", "OP_COMPRESS", "OP_MS_ID", "OP_SEGMENT", "OP_CC_MASK", "OP_CC_MESH",
     "msc_launch_count", "msc_trace_enable", "msc_trace_reset", "msc_trace_collect",
+    "Tune", "msc_batch_workspace_bytes", "msc_batch_segment", "msc_batch_plan_create", "msc_batch_plan_launch",
+    "msc_batch_plan_kernels", "msc_batch_plan_destroy", "msc_batch_autotune", "Batch",
 ]
 
 OK, ERR_ARG, ERR_WS, ERR_CUDA, ERR_NAN, ERR_NOT_CONVERGED, ERR_BUDGET, ERR_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
@@ -48,6 +50,11 @@ class MSCError(RuntimeError):
 
 class Grid(ctypes.Structure):
     _fields_ = [("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32)]
+
+
+class Tune(ctypes.Structure):
+    """msc_tune: steepest_shape (-1 = tuned/default, 0..3), build_shift (0 = tuned/default, 1..30)."""
+    _fields_ = [("steepest_shape", ctypes.c_int32), ("build_shift", ctypes.c_int32)]
 
 
 _lib = None
@@ -84,6 +91,15 @@ def load(build_if_missing: bool = False):
         "msc_trace_enable": (None, [ctypes.c_int]),
         "msc_trace_reset": (None, []),
         "msc_trace_collect": (ctypes.c_int, [ctypes.c_char_p, SZ]),
+        "msc_batch_workspace_bytes": (SZ, [P, I32]),
+        "msc_batch_segment": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, SZ, P, P, P]),
+        "msc_batch_plan_create": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, SZ, P, P, P,
+                                                 ctypes.POINTER(ctypes.c_void_p)]),
+        "msc_batch_plan_launch": (ctypes.c_int, [P, P]),
+        "msc_batch_plan_kernels": (ctypes.c_int, [P]),
+        "msc_batch_plan_destroy": (None, [P]),
+        "msc_batch_autotune": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, SZ, P, P, I32,
+                                              ctypes.POINTER(Tune), ctypes.POINTER(ctypes.c_float)]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -193,6 +209,66 @@ def msc_trace_collect() -> dict:
     if code != OK:
         raise MSCError(code, "msc_trace_collect")
     return {k: (int(v[0]), float(v[1])) for k, v in json.loads(buf.value.decode()).items()}
+
+
+def _grids(dims_list):
+    arr = (Grid * max(len(dims_list), 1))()
+    for i, d in enumerate(dims_list):
+        arr[i] = _grid(d)
+    return arr
+
+
+def _tune(tune):
+    if tune is None:
+        return None
+    if isinstance(tune, Tune):
+        return ctypes.byref(tune)
+    shape, shift = tune
+    return ctypes.byref(Tune(int(shape), int(shift)))
+
+
+def msc_batch_workspace_bytes(dims_list) -> int:
+    return int(load().msc_batch_workspace_bytes(_grids(dims_list), len(dims_list)))
+
+
+def msc_batch_segment(dims_list, f, order, asc, desc, ms, num_cells, ws, ws_bytes, tune, status,
+                      stream=None) -> int:
+    return load().msc_batch_segment(_grids(dims_list), len(dims_list), _p(f), _p(order), _p(asc), _p(desc),
+                                    _p(ms), _p(num_cells), _p(ws), ws_bytes, _tune(tune), _p(status),
+                                    _stream(stream))
+
+
+def msc_batch_plan_create(dims_list, f, order, asc, desc, ms, num_cells, ws, ws_bytes, tune, status,
+                          stream=None):
+    """Returns (code, plan handle as int)."""
+    h = ctypes.c_void_p()
+    code = load().msc_batch_plan_create(_grids(dims_list), len(dims_list), _p(f), _p(order), _p(asc), _p(desc),
+                                        _p(ms), _p(num_cells), _p(ws), ws_bytes, _tune(tune), _p(status),
+                                        _stream(stream), ctypes.byref(h))
+    return code, (h.value or 0)
+
+
+def msc_batch_plan_launch(plan: int, stream=None) -> int:
+    return load().msc_batch_plan_launch(plan, _stream(stream))
+
+
+def msc_batch_plan_kernels(plan: int) -> int:
+    return int(load().msc_batch_plan_kernels(plan))
+
+
+def msc_batch_plan_destroy(plan: int) -> None:
+    load().msc_batch_plan_destroy(plan)
+
+
+def msc_batch_autotune(dims_list, f, order, asc, desc, ms, num_cells, ws, ws_bytes, status, reps=2,
+                       stream=None):
+    """Returns (code, Tune, mean ms of the winner)."""
+    best = Tune(-1, 0)
+    t = ctypes.c_float(0.0)
+    code = load().msc_batch_autotune(_grids(dims_list), len(dims_list), _p(f), _p(order), _p(asc), _p(desc),
+                                     _p(ms), _p(num_cells), _p(ws), ws_bytes, _p(status), _stream(stream),
+                                     int(reps), ctypes.byref(best), ctypes.byref(t))
+    return code, best, float(t.value)
 
 
 # ---------------------------------------------------------------------------
@@ -336,3 +412,70 @@ def cc_mesh(row: torch.Tensor, col: torch.Tensor) -> torch.Tensor:
     _check(msc_cc_mesh(row, col, n, lab, ws, ws.numel(), st), "msc_cc_mesh")
     _finish(st, "msc_cc_mesh")
     return lab
+
+
+class Batch:
+    """A batch of grids packed into one vertex space with its outputs and
+    workspace (torch CUDA tensors), run by plain launches (``run``) or a
+    captured CUDA graph (``plan`` then ``launch``).  Outputs are
+    instance-local: ``split`` cuts a packed array into per-instance views."""
+
+    def __init__(self, dims_list, device="cuda"):
+        self.dims = [tuple(int(x) for x in d) for d in dims_list]
+        self.sizes = [d[0] * d[1] * d[2] for d in self.dims]
+        self.offsets = [0]
+        for n in self.sizes:
+            self.offsets.append(self.offsets[-1] + n)
+        self.total = self.offsets[-1]
+        dev = torch.device(device)
+        self.f = torch.empty(self.total, dtype=torch.float32, device=dev)
+        self.order, self.asc, self.desc, self.ms = (torch.empty(max(self.total, 1), dtype=torch.int32, device=dev)
+                                                    for _ in range(4))
+        self.num_cells = torch.empty(len(self.dims), dtype=torch.int32, device=dev)
+        nbytes = msc_batch_workspace_bytes(self.dims)
+        if nbytes == 0:
+            raise MSCError(ERR_ARG, "Batch: invalid grids")
+        self.ws = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+        self.status = torch.empty(1, dtype=torch.int32, device=dev)
+        self._plan = 0
+
+    def _bufs(self):
+        return (self.f, self.order, self.asc, self.desc, self.ms, self.num_cells, self.ws, self.ws.numel())
+
+    def run(self, tune=None, sync=True):
+        _check(msc_batch_segment(self.dims, *self._bufs(), tune, self.status), "msc_batch_segment")
+        if sync:
+            _finish(self.status, "msc_batch_segment")
+
+    def plan(self, tune=None):
+        self.close()
+        code, h = msc_batch_plan_create(self.dims, *self._bufs(), tune, self.status)
+        _check(code, "msc_batch_plan_create")
+        self._plan = h
+        return msc_batch_plan_kernels(h)
+
+    def launch(self, sync=True):
+        if not self._plan:
+            raise MSCError(ERR_ARG, "Batch.launch: no plan (call plan() first)")
+        _check(msc_batch_plan_launch(self._plan), "msc_batch_plan_launch")
+        if sync:
+            _finish(self.status, "msc_batch_plan_launch")
+
+    def autotune(self, reps=2):
+        code, best, ms = msc_batch_autotune(self.dims, *self._bufs(), self.status, reps)
+        _check(code, "msc_batch_autotune")
+        return (best.steepest_shape, best.build_shift), ms
+
+    def split(self, t: torch.Tensor):
+        return [t[a:b] for a, b in zip(self.offsets[:-1], self.offsets[1:])]
+
+    def close(self):
+        if self._plan:
+            msc_batch_plan_destroy(self._plan)
+            self._plan = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

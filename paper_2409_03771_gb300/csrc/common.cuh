@@ -71,6 +71,11 @@ class TraceScope {
     cudaEvent_t a_ = nullptr, b_ = nullptr;
 };
 
+// Launch counter adjustments: kernels recorded into a CUDA graph are
+// counted when the graph is replayed, not when they are captured.
+void add_launches(long long k);
+unsigned long long launch_count();
+
 // Properties of the current device (cached per device id).
 const Device& current_device();
 

@@ -274,7 +274,8 @@ MsScratch carve_ms_scratch(Carver& c, int64_t n) {
 }
 
 int run_ms_id(const int32_t* asc, const int32_t* desc, int32_t n, int32_t* ms, int32_t* num_cells,
-              const MsScratch& sc, bool counts_known, int32_t* status, cudaStream_t s) {
+              const MsScratch& sc, bool counts_known, int32_t* status, cudaStream_t s,
+              const unsigned long long** sorted_keys) {
     if (n <= 0) {
         MSC_TRY(cudaMemsetAsync(num_cells, 0, sizeof(int32_t), s));
         return MSC_OK;
@@ -313,6 +314,7 @@ int run_ms_id(const int32_t* asc, const int32_t* desc, int32_t n, int32_t* ms, i
                          reinterpret_cast<const int32_t*>(sc.ctl + 3), n, key_bits, sc.sort, status, s,
                          &in_alt);
     if (r) return r;
+    if (sorted_keys) *sorted_keys = in_alt ? sc.ukeys[1] : sc.ukeys[0];
     {
         TraceScope ts_("msid.rank", s);
         k_ms_rank<<<grid_for(n), kThreads, 0, s>>>(in_alt ? sc.uvals[1] : sc.uvals[0], sc.ctl, sc.table_vals, status);

@@ -23,7 +23,10 @@ MsScratch carve_ms_scratch(Carver& c, int64_t n);
 // When `counts_known` is false the labels are validated (in range, every
 // label labels itself) and the extrema counted first; otherwise ctl[0..1]
 // must already hold the number of minima and maxima.
+// `sorted_keys` (optional) receives the device array of the K distinct
+// pair keys asc * n + desc in ascending order (K = ctl[3]).
 int run_ms_id(const int32_t* asc, const int32_t* desc, int32_t n, int32_t* ms, int32_t* num_cells,
-              const MsScratch& sc, bool counts_known, int32_t* status, cudaStream_t s);
+              const MsScratch& sc, bool counts_known, int32_t* status, cudaStream_t s,
+              const unsigned long long** sorted_keys = nullptr);
 
 }  // namespace msc

@@ -88,6 +88,57 @@ constexpr int kHistRun = 16;  // consecutive keys per thread in the histogram
 // digits over 16 consecutive keys (neighbouring grid values share their
 // high digits, so the skewed digits cost one update per run) into a
 // warp-private shared histogram; blocks then add theirs to the global one.
+// Loads the float keys f[i0 .. i0+cnt) (cnt <= 16; the rest become 0)
+// into k[], noting NaNs.
+__device__ __forceinline__ void load_float_keys16(const float* __restrict__ f, int64_t i0, int cnt,
+                                                  uint32_t (&k)[kHistRun], bool& saw_nan) {
+    if (cnt == kHistRun && ((uintptr_t)(f + i0) & 15) == 0) {
+#pragma unroll
+        for (int q = 0; q < kHistRun / 4; ++q) {
+            const float4 v = reinterpret_cast<const float4*>(f + i0)[q];
+            saw_nan |= is_nan_bits(v.x) | is_nan_bits(v.y) | is_nan_bits(v.z) | is_nan_bits(v.w);
+            k[4 * q + 0] = float_key(v.x);
+            k[4 * q + 1] = float_key(v.y);
+            k[4 * q + 2] = float_key(v.z);
+            k[4 * q + 3] = float_key(v.w);
+        }
+    } else {
+#pragma unroll
+        for (int j = 0; j < kHistRun; ++j) {
+            const float x = j < cnt ? f[i0 + j] : 0.f;
+            saw_nan |= j < cnt && is_nan_bits(x);
+            k[j] = float_key(x);
+        }
+    }
+}
+
+// Adds the digits of k[0 .. cnt) for `npass` passes to the histograms h
+// ([npass][256]), one shared atomic per run of equal digits.
+template <typename KeyT>
+__device__ __forceinline__ void count_runs(const KeyT (&k)[kHistRun], int cnt, int npass, uint32_t* h) {
+    for (int p = 0; p < npass; ++p, h += kBins) {
+        uint32_t cur = (uint32_t)(k[0] >> (8 * p)) & 255u, run = 1;
+#pragma unroll
+        for (int j = 1; j < kHistRun; ++j) {
+            if (j >= cnt) break;
+            const uint32_t d = (uint32_t)(k[j] >> (8 * p)) & 255u;
+            if (d == cur) {
+                ++run;
+            } else {
+                atomicAdd(&h[cur], run);
+                cur = d;
+                run = 1;
+            }
+        }
+        atomicAdd(&h[cur], run);
+    }
+}
+
+// Digit histograms for `npass` passes over n keys (keys read from `keys`,
+// or made from the float field `f`).  Each thread counts runs of equal
+// digits over 16 consecutive keys (neighbouring grid values share their
+// high digits, so the skewed digits cost one update per run) into a
+// warp-private shared histogram; blocks then add theirs to the global one.
 template <typename KeyT, bool FROM_F>
 __global__ void __launch_bounds__(256) k_hist(const KeyT* __restrict__ keys,
                                               const float* __restrict__ f, int64_t n_host,
@@ -105,45 +156,12 @@ __global__ void __launch_bounds__(256) k_hist(const KeyT* __restrict__ keys,
         KeyT k[kHistRun];
         const int cnt = (int)min((int64_t)kHistRun, n - i0);
         if constexpr (FROM_F) {
-            if (cnt == kHistRun && ((uintptr_t)(f + i0) & 15) == 0) {
-#pragma unroll
-                for (int q = 0; q < kHistRun / 4; ++q) {
-                    const float4 v = reinterpret_cast<const float4*>(f + i0)[q];
-                    saw_nan |= is_nan_bits(v.x) | is_nan_bits(v.y) | is_nan_bits(v.z) | is_nan_bits(v.w);
-                    k[4 * q + 0] = float_key(v.x);
-                    k[4 * q + 1] = float_key(v.y);
-                    k[4 * q + 2] = float_key(v.z);
-                    k[4 * q + 3] = float_key(v.w);
-                }
-            } else {
-#pragma unroll
-                for (int j = 0; j < kHistRun; ++j) {
-                    const float x = j < cnt ? f[i0 + j] : 0.f;
-                    saw_nan |= j < cnt && is_nan_bits(x);
-                    k[j] = float_key(x);
-                }
-            }
+            load_float_keys16(f, i0, cnt, k, saw_nan);
         } else {
 #pragma unroll
             for (int j = 0; j < kHistRun; ++j) k[j] = j < cnt ? keys[i0 + j] : KeyT(0);
         }
-        for (int p = 0; p < npass; ++p) {
-            uint32_t* h = wsh + p * kBins;
-            uint32_t cur = (uint32_t)(k[0] >> (8 * p)) & 255u, run = 1;
-#pragma unroll
-            for (int j = 1; j < kHistRun; ++j) {
-                if (j >= cnt) break;
-                const uint32_t d = (uint32_t)(k[j] >> (8 * p)) & 255u;
-                if (d == cur) {
-                    ++run;
-                } else {
-                    atomicAdd(&h[cur], run);
-                    cur = d;
-                    run = 1;
-                }
-            }
-            atomicAdd(&h[cur], run);
-        }
+        count_runs(k, cnt, npass, wsh);
     }
     if (saw_nan) record_error(status, MSC_ERR_NAN);
     __syncthreads();
@@ -152,6 +170,66 @@ __global__ void __launch_bounds__(256) k_hist(const KeyT* __restrict__ keys,
         for (int w = 0; w < kWarps; ++w) c += sh[w * npass * kBins + i];
         if (c) atomicAdd(&hist[i], c);
     }
+}
+
+// Per-segment histograms of the float keys for the 4 passes of a
+// segmented sort: hist[seg][pass][256].  Block b takes a contiguous run of
+// tiles (one tile = 256 threads x 16 keys, inside one segment) and adds
+// its warp-private shared counts to the segment's global histogram each
+// time the segment changes and at the end.
+constexpr int kSegPasses = 4;
+
+__global__ void __launch_bounds__(256) k_hist_seg(const float* __restrict__ f,
+                                                  const int32_t* __restrict__ tile_seg,
+                                                  const int32_t* __restrict__ seg_off,
+                                                  const int32_t* __restrict__ seg_tile0, int64_t tiles,
+                                                  uint32_t* __restrict__ hist, int32_t* status) {
+    extern __shared__ uint32_t sh[];  // [kWarps][4][256]
+    constexpr int kSeg = kSegPasses * kBins;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    for (int i = tid; i < kWarps * kSeg; i += blockDim.x) sh[i] = 0;
+    __syncthreads();
+    uint32_t* wsh = sh + warp * kSeg;
+    const int64_t t0 = tiles * blockIdx.x / gridDim.x, t1 = tiles * (blockIdx.x + 1) / gridDim.x;
+    bool saw_nan = false;
+    auto flush = [&](int seg) {
+        __syncthreads();
+        for (int i = tid; i < kSeg; i += blockDim.x) {
+            uint32_t c = 0;
+            for (int w = 0; w < kWarps; ++w) {
+                c += sh[w * kSeg + i];
+                sh[w * kSeg + i] = 0;
+            }
+            if (c) atomicAdd(&hist[(int64_t)seg * kSeg + i], c);
+        }
+        __syncthreads();
+    };
+    int cur = t0 < t1 ? tile_seg[t0] : 0;
+    for (int64_t t = t0; t < t1; ++t) {
+        const int seg = tile_seg[t];  // uniform over the block
+        if (seg != cur) {
+            flush(cur);
+            cur = seg;
+        }
+        const int64_t off = seg_off[seg], n = seg_off[seg + 1] - off;
+        const int64_t i0 = (t - seg_tile0[seg]) * kSortTile + (int64_t)tid * kHistRun;
+        if (i0 < n) {
+            uint32_t k[kHistRun];
+            const int cnt = (int)min((int64_t)kHistRun, n - i0);
+            load_float_keys16(f + off, i0, cnt, k, saw_nan);
+            count_runs(k, cnt, kSegPasses, wsh);
+        }
+    }
+    if (t0 < t1) flush(cur);
+    if (saw_nan) record_error(status, MSC_ERR_NAN);
+}
+
+// hist[seg][pass][.] -> exclusive bin starts, one block per (seg, pass).
+__global__ void __launch_bounds__(256) k_seg_bstart(uint32_t* hist) {
+    __shared__ uint32_t s_w[kWarps];
+    uint32_t* h = hist + (int64_t)blockIdx.x * kBins;
+    const uint32_t c = h[threadIdx.x];
+    h[threadIdx.x] = block_scan_256(c, s_w) - c;
 }
 
 template <typename KeyT>
@@ -170,6 +248,14 @@ struct PassArgs {
     uint32_t* tile_counter;
     uint32_t epoch;
     int32_t* status;
+    // segmented sort (packed instances): segment of each tile, key offset
+    // of each segment, first tile of each segment; `hist` then holds the
+    // per-segment exclusive bin starts with a stride of seg_stride words
+    const int32_t* tile_seg;
+    const int32_t* seg_off;
+    const int32_t* seg_tile0;
+    int64_t seg_tiles;
+    int seg_stride;
 };
 
 template <typename KeyT, bool STAGE>
@@ -181,7 +267,12 @@ constexpr size_t pass_smem_bytes() {
 // One onesweep digit pass.  FROM_F: keys come from the float field and
 // the payload is the vertex id.  TO_ORDER: write order[payload] = position
 // instead of the sorted (key, payload) arrays.
-template <typename KeyT, bool FROM_F, bool TO_ORDER>
+//
+// SEG: the keys are packed segments sorted independently (batched
+// instances).  Tiles never straddle two segments, the look-back stops at
+// the segment's first tile, bin starts come per segment, and positions are
+// segment-local (keys land at seg_off + position; order gets the position).
+template <typename KeyT, bool FROM_F, bool TO_ORDER, bool SEG = false>
 __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem);  // [kWarps][256]
@@ -194,9 +285,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
     int32_t* s_vals = reinterpret_cast<int32_t*>(s_keys + kSortTile);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t n = a.d_n ? (int64_t)*a.d_n : a.n;
-    const int64_t ntiles = (n + kSortTile - 1) / kSortTile;
-    {
+    const int64_t n_all = a.d_n ? (int64_t)*a.d_n : a.n;
+    const int64_t ntiles = SEG ? a.seg_tiles : (n_all + kSortTile - 1) / kSortTile;
+    if constexpr (!SEG) {
         const uint32_t c = a.hist[tid];
         s_bstart[tid] = block_scan_256(c, s_misc + 1) - c;
     }
@@ -206,7 +297,16 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
         __syncthreads();
         const int64_t tile = s_misc[0];
         if (tile >= ntiles) break;
-        const int64_t base = tile * kSortTile + warp * (kItems * 32);
+        // this tile's segment: key offset, key count, tile index within it
+        int64_t seg_base = 0, n = n_all, ltile = tile;
+        if constexpr (SEG) {
+            const int seg = a.tile_seg[tile];
+            seg_base = a.seg_off[seg];
+            n = a.seg_off[seg + 1] - seg_base;
+            ltile = tile - a.seg_tile0[seg];
+            s_bstart[tid] = a.hist[(int64_t)seg * a.seg_stride + tid];  // read by this thread only
+        }
+        const int64_t base = ltile * kSortTile + warp * (kItems * 32);
 
         KeyT key[kItems];
         int32_t val[kItems];
@@ -215,12 +315,13 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
         for (int k = 0; k < kItems; ++k) {
             const int64_t idx = base + k * 32 + lane;
             if (idx < n) {
+                const int64_t gidx = seg_base + idx;
                 if constexpr (FROM_F) {
-                    key[k] = (KeyT)float_key(a.f_in[idx]);
-                    val[k] = (int32_t)idx;
+                    key[k] = (KeyT)float_key(a.f_in[gidx]);
+                    val[k] = (int32_t)gidx;
                 } else {
-                    key[k] = a.keys_in[idx];
-                    val[k] = a.vals_in[idx];
+                    key[k] = a.keys_in[gidx];
+                    val[k] = a.vals_in[gidx];
                 }
             } else {
                 key[k] = 0;
@@ -267,9 +368,9 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
         {
             unsigned long long* lb = a.lookback + (size_t)tile * kBins + tid;
             const unsigned long long ep = (unsigned long long)a.epoch << 32;
-            st_volatile_u64(lb, (tile == 0 ? kFlagInc : kFlagAgg) | ep | run);
+            st_volatile_u64(lb, (ltile == 0 ? kFlagInc : kFlagAgg) | ep | run);
             uint32_t excl = 0;
-            if (tile > 0) {
+            if (ltile > 0) {  // the segment's first tile publishes inclusive: the walk ends there
                 int64_t j = tile - 1;
                 uint32_t spins = 0;
                 while (j >= 0) {
@@ -300,7 +401,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
                 const uint32_t d = rk[k] >> 16;
                 if (d < 256u) {
                     const uint32_t pos = s_gbase[d] + s_whist[warp * kBins + d] + (rk[k] & 0xffffu);
-                    MSC_GUARD((uint32_t)val[k] < (uint64_t)n && pos < (uint64_t)n, a.status, -101)
+                    MSC_GUARD((uint32_t)val[k] < (uint64_t)(SEG ? a.n : n) && pos < (uint64_t)n, a.status, -101)
                     a.order_out[val[k]] = (int32_t)pos;
                 }
             }
@@ -326,14 +427,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
                 }
             }
             __syncthreads();
-            const int cnt = (int)min((int64_t)kSortTile, n - tile * kSortTile);
+            const int cnt = (int)min((int64_t)kSortTile, n - ltile * kSortTile);
             for (int i = tid; i < cnt; i += kThreads) {
                 const KeyT kk = s_keys[i];
                 const uint32_t d = (uint32_t)(kk >> a.shift) & 255u;
                 const uint32_t pos = s_gbase[d] + (uint32_t)i - s_excl[d];
                 MSC_GUARD(pos < (uint64_t)n, a.status, -102) {
-                    a.keys_out[pos] = kk;
-                    a.vals_out[pos] = s_vals[i];
+                    a.keys_out[seg_base + pos] = kk;
+                    a.vals_out[seg_base + pos] = s_vals[i];
                 }
             }
         }
@@ -341,10 +442,10 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
     }
 }
 
-template <typename KeyT, bool FROM_F, bool TO_ORDER>
+template <typename KeyT, bool FROM_F, bool TO_ORDER, bool SEG = false>
 int launch_pass(const PassArgs<KeyT>& a, int64_t max_n, cudaStream_t s, const char* label) {
     constexpr size_t smem = pass_smem_bytes<KeyT, !TO_ORDER>();
-    auto kern = k_onesweep<KeyT, FROM_F, TO_ORDER>;
+    auto kern = k_onesweep<KeyT, FROM_F, TO_ORDER, SEG>;
     static int configured_dev = -1;  // the attribute is set once per device
     if (configured_dev != current_device().id) {
         MSC_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -352,7 +453,7 @@ int launch_pass(const PassArgs<KeyT>& a, int64_t max_n, cudaStream_t s, const ch
     }
     int occ = 0;
     MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
-    const int64_t ntiles = ceil_div(max_n, kSortTile);
+    const int64_t ntiles = SEG ? a.seg_tiles : ceil_div(max_n, kSortTile);
     const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)current_device().sms * std::max(occ, 1)));
     {
         TraceScope ts_(label, s);
@@ -460,6 +561,88 @@ int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_
     a.tile_counter = sc.tile_counters + 3;
     a.epoch = 4;
     return launch_pass<uint32_t, false, true>(a, n, s, "order.pass_last");
+}
+
+void size_seg_sort_scratch(Sizer& s, int count, int64_t tiles) {
+    s.take<uint32_t>((size_t)count * kSegPasses * kBins + 8);
+    s.take<unsigned long long>((size_t)std::max<int64_t>(1, tiles) * kBins);
+}
+
+SortScratch carve_seg_sort_scratch(Carver& c, int count, int64_t tiles) {
+    SortScratch sc;
+    const size_t hist_words = (size_t)count * kSegPasses * kBins;
+    sc.hist = c.take<uint32_t>(hist_words + 8);
+    sc.tile_counters = sc.hist + hist_words;
+    sc.max_tiles = std::max<int64_t>(1, tiles);
+    sc.lookback = c.take<unsigned long long>((size_t)sc.max_tiles * kBins);
+    return sc;
+}
+
+int run_order_seg(const float* f, const SegTable& t, int32_t* order, uint32_t* key_a, int32_t* id_a,
+                  uint32_t* key_b, int32_t* id_b, const SortScratch& sc, int32_t* status,
+                  cudaStream_t s) {
+    if (t.tiles <= 0) return MSC_OK;
+    const size_t hist_words = (size_t)t.count * kSegPasses * kBins;
+    MSC_TRY(cudaMemsetAsync(sc.hist, 0, (hist_words + 8) * sizeof(uint32_t), s));
+    MSC_TRY(cudaMemsetAsync(sc.lookback, 0, (size_t)t.tiles * kBins * sizeof(unsigned long long), s));
+    int r = configure_hist();
+    if (r) return r;
+    {
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(t.tiles, (int64_t)current_device().sms * 4));
+        TraceScope ts_("order.hist", s);
+        k_hist_seg<<<grid, 256, hist_smem(kSegPasses), s>>>(f, t.tile_seg, t.off, t.tile0, t.tiles, sc.hist, status);
+    }
+    MSC_LAUNCHED();
+    {
+        TraceScope ts_("order.bstart", s);
+        k_seg_bstart<<<(unsigned)(t.count * kSegPasses), 256, 0, s>>>(sc.hist);
+    }
+    MSC_LAUNCHED();
+    PassArgs<uint32_t> a{};
+    a.n = t.total;
+    a.status = status;
+    a.lookback = sc.lookback;
+    a.tile_seg = t.tile_seg;
+    a.seg_off = t.off;
+    a.seg_tile0 = t.tile0;
+    a.seg_tiles = t.tiles;
+    a.seg_stride = kSegPasses * kBins;
+    a.f_in = f;
+    a.keys_out = key_a;
+    a.vals_out = id_a;
+    a.hist = sc.hist;
+    a.shift = 0;
+    a.tile_counter = sc.tile_counters + 0;
+    a.epoch = 1;
+    if ((r = launch_pass<uint32_t, true, false, true>(a, t.total, s, "order.pass_first"))) return r;
+    uint32_t* kin = key_a;
+    int32_t* iin = id_a;
+    uint32_t* kout = key_b;
+    int32_t* iout = id_b;
+    for (int p = 1; p <= 2; ++p) {
+        a.f_in = nullptr;
+        a.keys_in = kin;
+        a.vals_in = iin;
+        a.keys_out = kout;
+        a.vals_out = iout;
+        a.hist = sc.hist + p * kBins;
+        a.shift = 8 * p;
+        a.tile_counter = sc.tile_counters + p;
+        a.epoch = (uint32_t)(p + 1);
+        if ((r = launch_pass<uint32_t, false, false, true>(a, t.total, s, "order.pass"))) return r;
+        std::swap(kin, kout);
+        std::swap(iin, iout);
+    }
+    a.keys_in = kin;
+    a.vals_in = iin;
+    a.keys_out = nullptr;
+    a.vals_out = nullptr;
+    a.order_out = order;
+    a.hist = sc.hist + 3 * kBins;
+    a.shift = 24;
+    a.tile_counter = sc.tile_counters + 3;
+    a.epoch = 4;
+    return launch_pass<uint32_t, false, true, true>(a, t.total, s, "order.pass_last");
 }
 
 int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* keys_alt,

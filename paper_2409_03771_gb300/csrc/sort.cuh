@@ -25,6 +25,28 @@ int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_
               uint32_t* key_b, int32_t* id_b, const SortScratch& sc, int32_t* status,
               cudaStream_t s);
 
+// Packed segments sorted independently (batched instances).  Segment i
+// holds keys [off[i], off[i+1]) and tiles [tile0[i], tile0[i+1]) of
+// kSortTile keys; tile_seg[t] is the segment of tile t.  Device arrays,
+// built once on the host; total < 2^31.
+struct SegTable {
+    const int32_t* off;       // [count + 1]
+    const int32_t* tile0;     // [count + 1]
+    const int32_t* tile_seg;  // [tiles]
+    int32_t count;
+    int64_t total;
+    int64_t tiles;
+};
+
+void size_seg_sort_scratch(Sizer& s, int count, int64_t tiles);
+SortScratch carve_seg_sort_scratch(Carver& c, int count, int64_t tiles);
+
+// order[v] = rank of (f[v], v) within v's segment, for every segment at
+// once (4 segmented onesweep passes).  Ping-pong buffers of `total` entries.
+int run_order_seg(const float* f, const SegTable& t, int32_t* order, uint32_t* key_a, int32_t* id_a,
+                  uint32_t* key_b, int32_t* id_b, const SortScratch& sc, int32_t* status,
+                  cudaStream_t s);
+
 // Stable sort of (keys, vals) by the low `key_bits` bits of keys.  The
 // count is read on the device from *d_count (<= max_count).  Returns, via
 // *result_in_alt, whether the sorted data ended in the alt buffers.

@@ -24,12 +24,29 @@
 namespace msc {
 namespace {
 
-constexpr int TX = 32, TY = 8, TZ = 8;
-constexpr int BX = TX + 8, BY = TY + 2, BZ = TZ + 2;
-constexpr int PLANE = BX * BY;  // 400
-constexpr int BOX = PLANE * BZ;  // 4000
 constexpr int kThreads = 256;
 constexpr uint32_t kWaitLimit = 1u << 22;
+
+// A tile of TX x TY x TZ vertices and its shared-memory box (4 halo cells
+// in x, keeping 16-byte alignment, 1 in y and z).  A thread takes four
+// consecutive x vertices in REPS z planes.
+template <int TX_, int TY_, int TZ_>
+struct Shape {
+    static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
+    static constexpr int BX = TX + 8, BY = TY + 2, BZ = TZ + 2;
+    static constexpr int PLANE = BX * BY;
+    static constexpr int BOX = PLANE * BZ;
+    static constexpr int XQ = TX / 4;            // threads along x
+    static constexpr int LAYER = XQ * TY;        // threads per z plane
+    static constexpr int ZL = kThreads / LAYER;  // z planes per pass
+    static constexpr int REPS = TZ / ZL;
+    static_assert(TX % 4 == 0 && kThreads % LAYER == 0 && TZ % ZL == 0, "tile shape");
+};
+using Tile = Shape<32, 8, 8>;  // single-grid kernels (TMA box 40 x 10 x 10)
+constexpr int TX = Tile::TX, TY = Tile::TY, TZ = Tile::TZ;
+constexpr int BX = Tile::BX, BY = Tile::BY, BZ = Tile::BZ;
+constexpr int PLANE = Tile::PLANE;  // 400
+constexpr int BOX = Tile::BOX;      // 4000
 
 // Neighbour codes 0..13 (matching the row reads below), 14 = the vertex.
 __constant__ int8_t c_off[15][3] = {
@@ -42,6 +59,7 @@ struct GridInfo {
     int32_t tx, ty;  // tiles along x and y
     int64_t ntiles;
     int vec_store;  // asc/desc rows can take int4 stores
+    int32_t off;    // id of the grid's first vertex (packed batches; else 0)
 };
 
 // Packed candidate: order * 16 + neighbour code.  Out-of-grid cells hold
@@ -90,29 +108,29 @@ __device__ __forceinline__ void load_row(const int* r, int (&o)[6]) {
     o[5] = r[4];
 }
 
-template <typename PK>
+template <typename PK, typename S = Tile>
 __device__ __forceinline__ void tile_compute(const int* buf, const GridInfo& g, int x0, int y0,
                                              int z0, const int32_t* s_off, int32_t* __restrict__ asc,
                                              int32_t* __restrict__ desc, uint32_t& nmin,
                                              uint32_t& nmax) {
     const int tid = threadIdx.x;
-    const int xq = tid & 7, ly = (tid >> 3) & 7, lzq = tid >> 6;
+    const int xq = tid % S::XQ, ly = (tid / S::XQ) % S::TY, lzq = tid / S::LAYER;
     const int gx0 = x0 + 4 * xq, gy = y0 + ly;
     if (gx0 >= g.nx || gy >= g.ny) return;
 #pragma unroll
-    for (int rep = 0; rep < 2; ++rep) {
-        const int lz = lzq + 4 * rep;
+    for (int rep = 0; rep < S::REPS; ++rep) {
+        const int lz = lzq + S::ZL * rep;
         const int gz = z0 + lz;
         if (gz >= g.nz) break;
-        const int* b = buf + (lz + 1) * PLANE + (ly + 1) * BX + 4 * xq + 4;
+        const int* b = buf + (lz + 1) * S::PLANE + (ly + 1) * S::BX + 4 * xq + 4;
         int A[6], B[6], C[6], D[6], E[6], F[6], G[6];
-        load_row(b - PLANE, A);
-        load_row(b - PLANE - BX, B);
-        load_row(b - BX, C);
+        load_row(b - S::PLANE, A);
+        load_row(b - S::PLANE - S::BX, B);
+        load_row(b - S::BX, C);
         load_row(b, D);
-        load_row(b + BX, E);
-        load_row(b + PLANE, F);
-        load_row(b + PLANE + BX, G);
+        load_row(b + S::BX, E);
+        load_row(b + S::PLANE, F);
+        load_row(b + S::PLANE + S::BX, G);
         int hi_code[4], lo_code[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -125,7 +143,7 @@ __device__ __forceinline__ void tile_compute(const int* buf, const GridInfo& g, 
                              pack<P>(F[j + 1], 11), pack<P>(G[j], 12),    pack<P>(G[j + 1], 13)};
             best_codes(c, hi_code[i], lo_code[i]);
         }
-        const int32_t v0 = gx0 + g.nx * (gy + g.ny * gz);  // n < 2^31
+        const int32_t v0 = g.off + gx0 + g.nx * (gy + g.ny * gz);  // total < 2^31
         int out_hi[4], out_lo[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -151,15 +169,16 @@ __device__ __forceinline__ void tile_compute(const int* buf, const GridInfo& g, 
     }
 }
 
+template <typename S = Tile>
 __device__ __forceinline__ void tile_coords(const GridInfo& g, int64_t tile, int& x0, int& y0,
                                             int& z0) {
     const int64_t txy = (int64_t)g.tx * g.ty;
     const int64_t tz = tile / txy;
     const int64_t r = tile - tz * txy;
     const int64_t ty = r / g.tx;
-    x0 = (int)((r - ty * g.tx) * TX);
-    y0 = (int)(ty * TY);
-    z0 = (int)(tz * TZ);
+    x0 = (int)((r - ty * g.tx) * S::TX);
+    y0 = (int)(ty * S::TY);
+    z0 = (int)(tz * S::TZ);
 }
 
 __device__ __forceinline__ bool box_crosses_border(const GridInfo& g, int x0, int y0, int z0) {
@@ -275,6 +294,84 @@ __global__ void __launch_bounds__(kThreads) k_steepest_ld(const int32_t* __restr
 }
 
 // ----------------------------------------------------------------------------
+// Batched grids packed one after another.  Persistent CTAs walk the tiles
+// of all instances (instance i owns tiles [tile0[i], tile0[i+1])); the
+// block's instance comes from a binary search over tile0 (in shared memory
+// when the table fits), the box is staged with plain coalesced loads (an
+// instance's rows need not be 16-byte aligned, so no TMA), and pointers
+// are packed ids (instance offset + local id).  ext[2i], ext[2i+1] count
+// the instance's minima and maxima.
+
+constexpr int kSmemTileTable = 2048;  // instances whose tile table goes to shared memory
+
+template <typename S>
+__device__ __forceinline__ void load_box(const int32_t* __restrict__ order, const GridInfo& g, int x0,
+                                         int y0, int z0, int* buf) {
+    for (int i = threadIdx.x; i < S::BOX; i += kThreads) {
+        const int lz = i / S::PLANE, r = i - lz * S::PLANE, ly = r / S::BX, lx = r - ly * S::BX;
+        const int gx = x0 - 4 + lx, gy = y0 - 1 + ly, gz = z0 - 1 + lz;
+        int val = -1;
+        if (gx >= 0 && gy >= 0 && gz >= 0 && gx < g.nx && gy < g.ny && gz < g.nz)
+            val = order[(int64_t)g.off + gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz)];
+        buf[i] = val;
+    }
+}
+
+template <typename PK, typename S>
+__global__ void __launch_bounds__(kThreads) k_steepest_batch(const int32_t* __restrict__ order,
+                                                            const BatchInst* __restrict__ inst,
+                                                            const int32_t* __restrict__ tile0, int count,
+                                                            int32_t* asc, int32_t* desc, uint32_t* ext) {
+    __shared__ alignas(16) int buf[S::BOX];
+    __shared__ int32_t s_off[15];
+    __shared__ int32_t s_tile0[kSmemTileTable + 1];
+    __shared__ int s_inst;
+    const int tid = threadIdx.x;
+    const bool smem_table = count <= kSmemTileTable;
+    if (smem_table)
+        for (int i = tid; i <= count; i += kThreads) s_tile0[i] = tile0[i];
+    __syncthreads();
+    const int32_t* t0 = smem_table ? s_tile0 : tile0;
+    const int64_t ntiles = t0[count];
+    int cur = -1;
+    GridInfo g{};
+    uint32_t nmin = 0, nmax = 0;
+    for (int64_t tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+        if (tid == 0) {  // largest i with t0[i] <= tile (empty instances own no tile)
+            int lo = 0, hi = count - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (t0[mid] <= tile) lo = mid; else hi = mid - 1;
+            }
+            s_inst = lo;
+        }
+        __syncthreads();
+        const int i = s_inst;
+        if (i != cur) {  // block-uniform
+            if (cur >= 0) flush_counts(nmin, nmax, ext + 2 * cur);
+            nmin = nmax = 0;
+            cur = i;
+            const BatchInst b = inst[i];
+            g.nx = b.nx;
+            g.ny = b.ny;
+            g.nz = b.nz;
+            g.off = b.off;
+            g.tx = (b.nx + S::TX - 1) / S::TX;
+            g.ty = (b.ny + S::TY - 1) / S::TY;
+            g.vec_store = b.vec;
+            if (tid < 15) s_off[tid] = c_off[tid][0] + g.nx * (c_off[tid][1] + g.ny * c_off[tid][2]);
+        }
+        int x0, y0, z0;
+        tile_coords<S>(g, tile - t0[i], x0, y0, z0);
+        load_box<S>(order, g, x0, y0, z0, buf);
+        __syncthreads();
+        tile_compute<PK, S>(buf, g, x0, y0, z0, s_off, asc, desc, nmin, nmax);
+        __syncthreads();
+    }
+    if (cur >= 0) flush_counts(nmin, nmax, ext + 2 * cur);
+}
+
+// ----------------------------------------------------------------------------
 // CSR variant: 8 lanes per vertex, each lane scans every 8th neighbour.
 
 constexpr int kCsrLanes = 8;
@@ -344,6 +441,7 @@ __global__ void __launch_bounds__(256) k_steepest_csr(const int32_t* __restrict_
 int run_steepest_grid(const int32_t* order, msc_grid gd, int32_t* asc, int32_t* desc,
                       uint32_t* extrema, int32_t* status, cudaStream_t s, bool allow_tma) {
     GridInfo g;
+    g.off = 0;
     g.nx = gd.nx;
     g.ny = gd.ny;
     g.nz = gd.nz;
@@ -377,6 +475,62 @@ int run_steepest_grid(const int32_t* order, msc_grid gd, int32_t* asc, int32_t* 
     }
     MSC_LAUNCHED();
     return MSC_OK;
+}
+
+namespace {
+
+template <typename S>
+int64_t tiles_of(msc_grid g) {
+    return ceil_div(g.nx, S::TX) * ceil_div(g.ny, S::TY) * ceil_div(g.nz, S::TZ);
+}
+
+template <typename S>
+int launch_batch(const int32_t* order, const BatchInst* inst, const int32_t* tile0, int count,
+                 int64_t ntiles, bool packed, int32_t* asc, int32_t* desc, uint32_t* ext, cudaStream_t s) {
+    auto kern = packed ? k_steepest_batch<int32_t, S> : k_steepest_batch<int64_t, S>;
+    int occ = 1;
+    MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
+    const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(ntiles, (int64_t)current_device().sms * std::max(occ, 1)));
+    {
+        TraceScope ts_("steepest.batch", s);
+        kern<<<(unsigned)grid, kThreads, 0, s>>>(order, inst, tile0, count, asc, desc, ext);
+    }
+    MSC_LAUNCHED();
+    return MSC_OK;
+}
+
+}  // namespace
+
+int steepest_batch_shapes() { return 4; }
+
+int64_t steepest_batch_tiles(int shape, msc_grid g) {
+    switch (shape) {
+        case 1: return tiles_of<Shape<16, 8, 16>>(g);
+        case 2: return tiles_of<Shape<64, 4, 8>>(g);
+        case 3: return tiles_of<Shape<16, 16, 8>>(g);
+        default: return tiles_of<Tile>(g);
+    }
+}
+
+const char* steepest_batch_shape_name(int shape) {
+    switch (shape) {
+        case 1: return "16x8x16";
+        case 2: return "64x4x8";
+        case 3: return "16x16x8";
+        default: return "32x8x8";
+    }
+}
+
+int run_steepest_batch(const int32_t* order, const BatchInst* inst, const int32_t* tile0, int count,
+                       int64_t ntiles, int shape, bool packed, int32_t* asc, int32_t* desc, uint32_t* ext,
+                       cudaStream_t s) {
+    if (ntiles <= 0) return MSC_OK;
+    switch (shape) {
+        case 1: return launch_batch<Shape<16, 8, 16>>(order, inst, tile0, count, ntiles, packed, asc, desc, ext, s);
+        case 2: return launch_batch<Shape<64, 4, 8>>(order, inst, tile0, count, ntiles, packed, asc, desc, ext, s);
+        case 3: return launch_batch<Shape<16, 16, 8>>(order, inst, tile0, count, ntiles, packed, asc, desc, ext, s);
+        default: return launch_batch<Tile>(order, inst, tile0, count, ntiles, packed, asc, desc, ext, s);
+    }
 }
 
 int run_steepest_csr(const int32_t* order, const int32_t* row, const int32_t* col, int32_t n,

@@ -48,6 +48,9 @@ cudaEvent_t take_event() {
 TraceScope::TraceScope(const char* label, cudaStream_t s) : label_(label), stream_(s) {
     g_launches.fetch_add(1, std::memory_order_relaxed);
     if (!g_on.load(std::memory_order_relaxed)) return;
+    cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(s, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone)
+        return;  // launches captured into a graph are not timed one by one
     std::lock_guard<std::mutex> lock(g_mu);
     a_ = take_event();
     b_ = take_event();
@@ -60,6 +63,12 @@ TraceScope::~TraceScope() {
     std::lock_guard<std::mutex> lock(g_mu);
     g_recs.push_back({label_, a_, b_});
 }
+
+void add_launches(long long k) {
+    g_launches.fetch_add((unsigned long long)k, std::memory_order_relaxed);
+}
+
+unsigned long long launch_count() { return g_launches.load(); }
 
 }  // namespace msc
 
