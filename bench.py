@@ -43,6 +43,8 @@ def parse_args():
     ap.add_argument("--mesh-edge", type=int, default=MESH_EDGE)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched measurement")
+    ap.add_argument("--batch-count", type=int, default=512)
     return ap.parse_args()
 
 
@@ -331,10 +333,99 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(f_smooth, f_noise, mask, E)
+    if not args.no_batch:
+        del f_smooth, f_noise, mask, row, col, seg_out, lab, mlab, ws
+        torch.cuda.empty_cache()
+        out["batch"] = batch_bench(dev, count=args.batch_count)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
         dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# batched segmentation: 512 anisotropic instances in one graph launch vs one
+# msc_segment launch sequence per instance
+
+
+BATCH_SEED0 = 100
+
+
+def batch_bench(dev, count=512, reps=5):
+    import torch
+
+    import paper_2409_03771_gb300 as msc
+    import workloads
+
+    t0 = time.time()
+    dims_list, fields = [], []
+    for i in range(count):
+        dims, f = workloads.batch_instance(BATCH_SEED0 + i, device=dev)
+        dims_list.append(dims)
+        fields.append(f.reshape(-1))
+    b = msc.Batch(dims_list, device=dev)
+    torch.cat(fields, out=b.f)
+    del fields
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    stream = torch.cuda.current_stream(dev)
+    (shape, shift), tuned_ms = b.autotune(reps=1)
+    kernels = b.plan()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        b.launch(sync=False)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        time.sleep(0.2)
+        ev0.record(stream)
+        for _ in range(reps):
+            b.launch(sync=False)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    graph_ms = ev0.elapsed_time(ev1) / reps
+    batch_status = int(b.status.item())
+    # the plain path: one msc_segment per instance, outputs in the same packed layout
+    nmax = max(b.sizes)
+    ws = torch.empty(msc.msc_workspace_bytes(msc.OP_SEGMENT, nmax), dtype=torch.uint8, device=dev)
+    outs = [torch.empty_like(t) for t in (b.order, b.asc, b.desc, b.ms)]
+    cells = torch.empty(count, dtype=torch.int32, device=dev)
+    st = torch.zeros(count, dtype=torch.int32, device=dev)
+
+    def plain():
+        for i, d in enumerate(dims_list):
+            a, z = b.offsets[i], b.offsets[i + 1]
+            r = msc.msc_segment(b.f[a:z], d, outs[0][a:z], outs[1][a:z], outs[2][a:z], outs[3][a:z],
+                                cells[i:i + 1], ws, ws.numel(), st[i:i + 1], stream)
+            assert r == 0, msc.msc_status_string(r)
+
+    plain()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(2):
+        plain()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    plain_ms = ev0.elapsed_time(ev1) / 2
+    if batch_status != 0 or int(st.abs().sum().item()) != 0:
+        raise RuntimeError("batched or plain segmentation reported a device error")
+    same = all(torch.equal(x[: b.total], y[: b.total]) for x, y in zip((b.order, b.asc, b.desc, b.ms), outs))
+    same = same and torch.equal(cells, b.num_cells)
+    out = {
+        "workload": (f"{count} instances (seeds {BATCH_SEED0}..{BATCH_SEED0 + count - 1}), edges "
+                     f"log-uniform in [16, 256] per axis, 8 Gaussians each; MS segmentation per instance"),
+        "vertices": b.total, "graph_ms": round(graph_ms, 3), "plain_ms": round(plain_ms, 3),
+        "graph_vertices_per_s": b.total / (graph_ms / 1e3), "plain_vertices_per_s": b.total / (plain_ms / 1e3),
+        "speedup_vs_plain": round(plain_ms / graph_ms, 3), "identical_to_plain": bool(same),
+        "kernels_per_graph": kernels, "plain_launches": None,
+        "tune": {"steepest_shape": shape, "build_shift": shift, "autotuned_ms": round(tuned_ms, 3)},
+        "cells_total": int(b.num_cells.sum().item()), "input_gen_s": round(gen_s, 1), "clocks": clk.summary(),
+    }
+    launches0 = msc.msc_launch_count()
+    plain()
+    torch.cuda.synchronize()
+    out["plain_launches"] = int(msc.msc_launch_count() - launches0)
+    b.close()
+    return out
 
 
 # ---------------------------------------------------------------------------

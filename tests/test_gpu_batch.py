@@ -159,3 +159,43 @@ def test_batch_many_instances_with_long_paths(m):
     b.launch()
     check(b, want)
     b.close()
+
+
+def test_batch_full_size_512_instances(m):
+    """The batched workload at full size: 512 anisotropic instances (seeds
+    100..611, edges 16..256 per axis, ~330M vertices) in one graph launch.
+    Every instance equals msc_segment on that grid alone, bit for bit; the
+    oracle checks the six smallest instances and two of median size."""
+    import oracle
+
+    dims_list, fields = [], []
+    for i in range(512):
+        dims, f = workloads.batch_instance(100 + i, device="cuda")
+        dims_list.append(dims)
+        fields.append(f.reshape(-1))
+    b = m.Batch(dims_list)
+    torch.cat(fields, out=b.f)
+    del fields
+    b.plan()
+    b.launch()
+    ws = torch.empty(m.msc_workspace_bytes(m.OP_SEGMENT, max(b.sizes)), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    k = torch.zeros(1, dtype=torch.int32, device="cuda")
+    outs = [torch.empty(max(b.sizes), dtype=torch.int32, device="cuda") for _ in range(4)]
+    batch_views = [b.split(t[: b.total]) for t in (b.order, b.asc, b.desc, b.ms)]
+    cells = b.num_cells.cpu().tolist()
+    for i, d in enumerate(dims_list):
+        n = b.sizes[i]
+        a, z = b.offsets[i], b.offsets[i + 1]
+        assert m.msc_segment(b.f[a:z], d, *(o[:n] for o in outs), k, ws, ws.numel(), st) == m.OK
+        for j in range(4):
+            assert torch.equal(outs[j][:n], batch_views[j][i]), (i, d, j)
+        assert int(k.item()) == cells[i] and int(st.item()) == m.OK
+    by_size = sorted(range(512), key=lambda i: b.sizes[i])
+    for i in by_size[:6] + by_size[255:257]:
+        f = b.f[b.offsets[i]:b.offsets[i + 1]].cpu().numpy()
+        wo, wa, wd, wm, wk = oracle.segment_grid(f, dims_list[i])
+        for got, want in zip((batch_views[j][i] for j in range(4)), (wo, wa, wd, wm)):
+            np.testing.assert_array_equal(got.cpu().numpy(), want)
+        assert cells[i] == wk
+    b.close()
