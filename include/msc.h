@@ -258,6 +258,89 @@ MSC_API int msc_batch_autotune(const msc_grid* grids, int32_t count, const float
                                size_t ws_bytes, int32_t* d_status, void* stream, int32_t reps,
                                msc_tune* best, float* best_ms);
 
+/* ---------------------------------------------------------------------
+ * Serving.  A server admits segmentation (msc_segment) and mask-CC
+ * (msc_cc_mask) requests of mixed sizes, runs them with continuous
+ * batching inside a fixed HBM budget and keeps each result on the device
+ * until the caller releases it.  The paper has no serving layer; every
+ * result is exactly what the single-request entry point returns for the
+ * same input, alone or in any mix.
+ *
+ * Scheduling: a server thread takes requests in arrival order.  A request
+ * is admitted when one of `slots` CUDA streams is free and its device
+ * memory (outputs + workspace, from an arena of `hbm_budget` bytes
+ * allocated at creation) fits; admission never skips ahead, so no request
+ * starves.  Consecutive waiting segmentation requests of at most
+ * `group_max_vertices` vertices each are admitted together and run as one
+ * batched launch (msc_batch_segment over a packed copy of their inputs);
+ * larger requests and CC requests run on their own.  A batched launch
+ * that reports a device error (e.g. a NaN in one field) is re-run request
+ * by request, so every request gets the status it would get alone.  Work
+ * on different
+ * slots overlaps on the GPU; a request that arrives while others run is
+ * admitted as soon as a slot and memory free up.  Results stay in the
+ * arena until msc_server_release. */
+
+#define MSC_JOB_SEGMENT 1
+#define MSC_JOB_CC_MASK 2
+
+typedef struct {
+    int32_t kind;      /* MSC_JOB_SEGMENT or MSC_JOB_CC_MASK */
+    msc_grid g;
+    int32_t conn;      /* MSC_JOB_CC_MASK: 6 or 14 */
+    const void* input; /* device float32[n] field (segment) or uint8[n] mask
+                          (CC), owned by the caller, unchanged until the
+                          request completes */
+} msc_job;
+
+typedef struct {
+    int32_t status;      /* MSC_PENDING, MSC_OK or the request's error */
+    int32_t num_cells;   /* segment: Morse-Smale cells; CC: 0 */
+    int64_t n;           /* vertices */
+    int32_t* order;      /* device, n entries, segment only (else NULL) */
+    int32_t* asc;
+    int32_t* desc;
+    int32_t* ms;
+    int32_t* label;      /* device, n entries, CC only (else NULL) */
+    double t_submit;     /* host steady-clock seconds: submitted, */
+    double t_start;      /* launched, */
+    double t_done;       /* and seen complete */
+    int32_t group_size;  /* requests that ran in the same launch */
+} msc_result;
+
+typedef struct msc_server msc_server;
+
+/* hbm_budget: bytes of the result/workspace arena (allocated here; the
+ * only allocation the server makes on the device).  slots: concurrent
+ * streams (1..16).  group_max_vertices: size limit for batching several
+ * segmentations into one launch (0 = never batch).  Returns NULL on a bad
+ * argument or when the arena cannot be allocated. */
+MSC_API msc_server* msc_server_create(size_t hbm_budget, int32_t slots, int64_t group_max_vertices);
+
+/* Queue a request; *ticket identifies it.  Returns MSC_ERR_ARG for a bad
+ * request and MSC_ERR_BUDGET when it could never fit the budget.  The
+ * call only queues: it returns at once. */
+MSC_API int msc_server_submit(msc_server* s, const msc_job* job, uint64_t* ticket);
+
+/* Copy the request's state into *out: status MSC_PENDING while it waits
+ * or runs.  msc_server_wait blocks up to timeout_ms (< 0: no limit) for
+ * completion and returns the same as msc_server_poll. */
+MSC_API int msc_server_poll(msc_server* s, uint64_t ticket, msc_result* out);
+MSC_API int msc_server_wait(msc_server* s, uint64_t ticket, double timeout_ms, msc_result* out);
+
+/* Free a completed request's device memory (its result pointers become
+ * invalid).  MSC_PENDING if it has not completed, MSC_ERR_ARG for an
+ * unknown ticket. */
+MSC_API int msc_server_release(msc_server* s, uint64_t ticket);
+
+/* Arena bytes in use and the number of requests queued, running, done. */
+MSC_API int msc_server_stats(msc_server* s, size_t* arena_used, int32_t* queued, int32_t* running,
+                             int32_t* done);
+
+/* Waits for the running work, then frees the arena, the streams and every
+ * result. */
+MSC_API void msc_server_destroy(msc_server* s);
+
 #ifdef __cplusplus
 }
 #endif

@@ -33,6 +33,8 @@ __all__ = [
     "msc_launch_count", "msc_trace_enable", "msc_trace_reset", "msc_trace_collect",
     "Tune", "msc_batch_workspace_bytes", "msc_batch_segment", "msc_batch_plan_create", "msc_batch_plan_launch",
     "msc_batch_plan_kernels", "msc_batch_plan_destroy", "msc_batch_autotune", "Batch",
+    "Job", "Result", "JOB_SEGMENT", "JOB_CC_MASK", "msc_server_create", "msc_server_submit", "msc_server_poll",
+    "msc_server_wait", "msc_server_release", "msc_server_stats", "msc_server_destroy", "Server",
 ]
 
 OK, ERR_ARG, ERR_WS, ERR_CUDA, ERR_NAN, ERR_NOT_CONVERGED, ERR_BUDGET, ERR_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
@@ -40,6 +42,7 @@ ERR_TOO_LARGE = -8
 NOALLOC_MAX_N = 1 << 22
 PENDING = 1
 OP_ORDER, OP_COMPRESS, OP_MS_ID, OP_SEGMENT, OP_CC_MASK, OP_CC_MESH = 1, 2, 3, 4, 5, 6
+JOB_SEGMENT, JOB_CC_MASK = 1, 2
 
 
 class MSCError(RuntimeError):
@@ -55,6 +58,19 @@ class Grid(ctypes.Structure):
 class Tune(ctypes.Structure):
     """msc_tune: steepest_shape (-1 = tuned/default, 0..3), build_shift (0 = tuned/default, 1..30)."""
     _fields_ = [("steepest_shape", ctypes.c_int32), ("build_shift", ctypes.c_int32)]
+
+
+class Job(ctypes.Structure):
+    """msc_job: one served request."""
+    _fields_ = [("kind", ctypes.c_int32), ("g", Grid), ("conn", ctypes.c_int32), ("input", ctypes.c_void_p)]
+
+
+class Result(ctypes.Structure):
+    """msc_result: a served request's state and device outputs."""
+    _fields_ = [("status", ctypes.c_int32), ("num_cells", ctypes.c_int32), ("n", ctypes.c_int64),
+                ("order", ctypes.c_void_p), ("asc", ctypes.c_void_p), ("desc", ctypes.c_void_p),
+                ("ms", ctypes.c_void_p), ("label", ctypes.c_void_p), ("t_submit", ctypes.c_double),
+                ("t_start", ctypes.c_double), ("t_done", ctypes.c_double), ("group_size", ctypes.c_int32)]
 
 
 _lib = None
@@ -100,6 +116,14 @@ def load(build_if_missing: bool = False):
         "msc_batch_plan_destroy": (None, [P]),
         "msc_batch_autotune": (ctypes.c_int, [P, I32, P, P, P, P, P, P, P, SZ, P, P, I32,
                                               ctypes.POINTER(Tune), ctypes.POINTER(ctypes.c_float)]),
+        "msc_server_create": (P, [SZ, I32, I64]),
+        "msc_server_submit": (ctypes.c_int, [P, ctypes.POINTER(Job), ctypes.POINTER(ctypes.c_uint64)]),
+        "msc_server_poll": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.POINTER(Result)]),
+        "msc_server_wait": (ctypes.c_int, [P, ctypes.c_uint64, ctypes.c_double, ctypes.POINTER(Result)]),
+        "msc_server_release": (ctypes.c_int, [P, ctypes.c_uint64]),
+        "msc_server_stats": (ctypes.c_int, [P, ctypes.POINTER(SZ), ctypes.POINTER(I32), ctypes.POINTER(I32),
+                                            ctypes.POINTER(I32)]),
+        "msc_server_destroy": (None, [P]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -473,6 +497,128 @@ class Batch:
         if self._plan:
             msc_batch_plan_destroy(self._plan)
             self._plan = 0
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ---------------------------------------------------------------------------
+# serving
+
+
+def msc_server_create(budget: int, slots: int = 4, group_max_vertices: int = 1 << 21) -> int:
+    return load().msc_server_create(budget, slots, group_max_vertices) or 0
+
+
+def msc_server_submit(srv: int, job: Job):
+    t = ctypes.c_uint64()
+    code = load().msc_server_submit(srv, ctypes.byref(job), ctypes.byref(t))
+    return code, int(t.value)
+
+
+def msc_server_poll(srv: int, ticket: int):
+    r = Result()
+    return load().msc_server_poll(srv, ticket, ctypes.byref(r)), r
+
+
+def msc_server_wait(srv: int, ticket: int, timeout_ms: float = -1.0):
+    r = Result()
+    return load().msc_server_wait(srv, ticket, float(timeout_ms), ctypes.byref(r)), r
+
+
+def msc_server_release(srv: int, ticket: int) -> int:
+    return load().msc_server_release(srv, ticket)
+
+
+def msc_server_stats(srv: int):
+    used, q, run, done = ctypes.c_size_t(), ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+    code = load().msc_server_stats(srv, ctypes.byref(used), ctypes.byref(q), ctypes.byref(run), ctypes.byref(done))
+    _check(code, "msc_server_stats")
+    return {"arena_used": used.value, "queued": q.value, "running": run.value, "done": done.value}
+
+
+def msc_server_destroy(srv: int) -> None:
+    load().msc_server_destroy(srv)
+
+
+class _DeviceArray:
+    """A device int32 array by address (zero-copy view through the CUDA array interface)."""
+
+    def __init__(self, ptr: int, n: int):
+        self.__cuda_array_interface__ = {"shape": (n,), "typestr": "<i4", "data": (ptr, False), "version": 2,
+                                         "strides": None}
+
+
+class Server:
+    """msc_server with torch inputs: submit fields / masks, wait, view the
+    device-resident outputs as torch tensors (valid until ``release``)."""
+
+    def __init__(self, budget: int, slots: int = 4, group_max_vertices: int = 1 << 21):
+        self.h = msc_server_create(int(budget), int(slots), int(group_max_vertices))
+        if not self.h:
+            raise MSCError(ERR_BUDGET, "msc_server_create (bad arguments or arena allocation failed)")
+        self._inputs = {}
+
+    def _submit(self, kind, t, dims, conn):
+        n = int(dims[0]) * int(dims[1]) * int(dims[2])
+        if t.numel() != n or not t.is_cuda or not t.is_contiguous():
+            raise MSCError(ERR_ARG, "submit: input must be a contiguous CUDA tensor of the grid's size")
+        code, ticket = msc_server_submit(self.h, Job(kind, _grid(dims), conn, t.data_ptr()))
+        _check(code, "msc_server_submit")
+        self._inputs[ticket] = t  # the input must outlive the request
+        return ticket
+
+    def submit_segment(self, f: torch.Tensor, dims) -> int:
+        return self._submit(JOB_SEGMENT, _flat(f, torch.float32), dims, 0)
+
+    def submit_cc(self, mask: torch.Tensor, dims, conn: int = 6) -> int:
+        return self._submit(JOB_CC_MASK, _flat(mask, torch.uint8), dims, conn)
+
+    def poll(self, ticket: int) -> Result:
+        code, r = msc_server_poll(self.h, ticket)
+        if code not in (OK, PENDING):
+            raise MSCError(code, "msc_server_poll")
+        return r
+
+    def wait(self, ticket: int, timeout_ms: float = -1.0) -> Result:
+        code, r = msc_server_wait(self.h, ticket, timeout_ms)
+        if code not in (OK, PENDING):
+            raise MSCError(code, "msc_server_wait")
+        return r
+
+    @staticmethod
+    def view(r: Result, field: str) -> torch.Tensor:
+        ptr = getattr(r, field)
+        if not ptr:
+            raise MSCError(ERR_ARG, f"result has no {field}")
+        return torch.as_tensor(_DeviceArray(ptr, int(r.n)), device="cuda")
+
+    def outputs(self, ticket: int) -> dict:
+        """Copies of the request's outputs (waits for it)."""
+        r = self.wait(ticket)
+        _check(r.status, "served request")
+        if r.label:
+            return {"label": self.view(r, "label").clone()}
+        out = {k: self.view(r, k).clone() for k in ("order", "asc", "desc", "ms")}
+        out["num_cells"] = int(r.num_cells)
+        return out
+
+    def release(self, ticket: int) -> None:
+        code = msc_server_release(self.h, ticket)
+        _check(code, "msc_server_release")
+        self._inputs.pop(ticket, None)
+
+    def stats(self) -> dict:
+        return msc_server_stats(self.h)
+
+    def close(self):
+        if self.h:
+            msc_server_destroy(self.h)
+            self.h = 0
+            self._inputs.clear()
 
     def __del__(self):
         try:

@@ -61,6 +61,14 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert m.msc_cc_mask(16, (4, 4, 4), 7, 16, 16, 256, 16, stream=0) == m.ERR_ARG
     assert m.msc_segment(16, (4, 4, 4), 16, 16, 16, 16, 16, 16, 10, 16, stream=0) == m.ERR_WS
     assert m.msc_compress(16, 10, 16, 0, 16, stream=0) == m.ERR_WS
+    # the batch and serving entry points check their arguments on the host too
+    assert m.msc_batch_workspace_bytes([(4, 4, 4), (2, 3, 5)]) > m.msc_batch_workspace_bytes([(4, 4, 4)]) > 0
+    assert m.msc_batch_workspace_bytes([(4, 4, 0)]) == 0
+    assert m.msc_batch_segment([(4, 4, 4)], 0, 0, 0, 0, 0, 0, 0, 0, None, 0, stream=0) == m.ERR_ARG
+    assert m.msc_batch_segment([(4, 4, 4)], 16, 16, 16, 16, 16, 16, 256, 10, (9, 0), 16, stream=0) == m.ERR_ARG
+    assert m.msc_server_create(0, 1, 0) == 0
+    assert m.msc_server_create(1 << 20, 0, 0) == 0
+    assert m.msc_server_submit(0, m.Job())[0] == m.ERR_ARG
 
 
 def test_no_cpu_fallback():
