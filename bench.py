@@ -45,6 +45,8 @@ def parse_args():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched measurement")
     ap.add_argument("--batch-count", type=int, default=512)
+    ap.add_argument("--no-serve", action="store_true", help="skip the served-request rate sweep")
+    ap.add_argument("--serve-requests", type=int, default=64, help="requests per arrival rate")
     return ap.parse_args()
 
 
@@ -337,6 +339,9 @@ def run_ours(args):
         del f_smooth, f_noise, mask, row, col, seg_out, lab, mlab, ws
         torch.cuda.empty_cache()
         out["batch"] = batch_bench(dev, count=args.batch_count)
+    if not args.no_serve:
+        torch.cuda.empty_cache()
+        out["serve"] = serve_bench(dev, args.serve_requests)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -429,27 +434,112 @@ def batch_bench(dev, count=512, reps=5):
 
 
 # ---------------------------------------------------------------------------
+# serving: Poisson arrivals of mixed segmentation / mask-CC requests
+
+
+SERVE_RATES = (100, 300, 1000, 3000, 10000)
+SERVE_POOL = 48          # distinct seeded requests; request i takes pool[i % 48]
+SERVE_SEED0 = 5000
+SERVE_BUDGET = 120 << 30
+
+
+def serve_pool(dev):
+    import workloads
+
+    pool = []
+    for j in range(SERVE_POOL):
+        kind, edge, rng = workloads.serve_request(SERVE_SEED0 + j)
+        t = workloads.serve_field(kind, edge, rng, device=dev).reshape(-1).contiguous()
+        pool.append((kind, (edge, edge, edge), t))
+    return pool
+
+
+def serve_run(msc, pool, rate, count, slots, group_max):
+    import numpy as np
+
+    srv = msc.Server(SERVE_BUDGET, slots=slots, group_max_vertices=group_max)
+    rng = np.random.default_rng(rate)
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
+    tickets, verts = [], 0
+    t0 = time.perf_counter()
+    for i in range(count):
+        kind, dims, t = pool[i % len(pool)]
+        delay = t0 + arrivals[i] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        tickets.append(srv.submit_segment(t, dims) if kind == "segment" else srv.submit_cc(t, dims, 6))
+        verts += t.numel()
+    res = [srv.wait(tk) for tk in tickets]
+    if any(r.status != msc.OK for r in res):
+        raise RuntimeError(f"served request failed: {[r.status for r in res if r.status]}")
+    lat = np.array([(r.t_done - r.t_submit) * 1e3 for r in res])
+    span = max(r.t_done for r in res) - min(r.t_submit for r in res)
+    out = {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+           "vertices_per_s": verts / span, "requests_per_s": count / span,
+           "mean_group": round(float(np.mean([r.group_size for r in res])), 2)}
+    for tk in tickets:
+        srv.release(tk)
+    srv.close()
+    return out
+
+
+def serve_bench(dev, count):
+    import torch
+
+    import paper_2409_03771_gb300 as msc
+
+    t0 = time.time()
+    pool = serve_pool(dev)
+    torch.cuda.synchronize()
+    gen_s = time.time() - t0
+    serve_run(msc, pool, 1000, 8, 4, 1 << 21)  # warm-up: library state, allocator
+    rates = []
+    with ClockSampler(dev.index) as clk:
+        for rate in SERVE_RATES:
+            row = {"rate": rate}
+            row.update(serve_run(msc, pool, rate, count, slots=4, group_max=1 << 21))
+            row["plain"] = serve_run(msc, pool, rate, count, slots=1, group_max=0)
+            rates.append(row)
+    seg = [t.numel() for k, _, t in pool if k == "segment"]
+    cc = [t.numel() for k, _, t in pool if k == "cc"]
+    return {
+        "workload": (f"Poisson arrivals, {count} requests per rate, drawn from {SERVE_POOL} seeded requests "
+                     f"(seeds {SERVE_SEED0}..{SERVE_SEED0 + SERVE_POOL - 1}): 70% MS segmentation of a cube with "
+                     f"edge log-uniform in [32, 512], 30% 6-conn mask CC with edge log-uniform in [64, 768]"),
+        "budget_gb": SERVE_BUDGET >> 30, "server": "4 stream slots, segmentations <= 2^21 vertices batched",
+        "plain": "1 slot, one request per launch sequence, no batching",
+        "pool_mean_vertices": {"segment": int(sum(seg) / max(1, len(seg))), "cc": int(sum(cc) / max(1, len(cc)))},
+        "latency": "host submit to completion seen by the server (completion callback)",
+        "rates": rates, "input_gen_s": round(gen_s, 1), "clocks": clk.summary(),
+    }
+
+
+# ---------------------------------------------------------------------------
 # CPU oracle (baseline and reference arm)
 
 
-SAMPLE_MESH_EDGE = 96
+# (field z-planes, mask z-planes, mesh edge) of the oracle samples: the CPU
+# baseline takes ~10 s of single-core work, a reference-arm step ~1 s
+BASELINE_SAMPLE = (96, 192, 128)
+STEP_SAMPLE = (8, 16, 96)
 
 
-def oracle_sample(f_smooth, f_noise, mask, E):
-    """Host copies of a bounded sample of the step's workload (a few seconds
-    of single-core oracle work): 8 z-planes of each field (a 512x512x8 grid),
-    16 z-planes of the mask, and a 96^3 mesh made with the same recipe."""
+def oracle_sample(f_smooth, f_noise, mask, E, size=STEP_SAMPLE):
+    """Host copies of a bounded sample of the step's workload: the first zs
+    z-planes of each field, zm z-planes of the mask, and a mesh of the same
+    recipe with the given edge."""
     import workloads
 
-    zs, zm = 8, 16
+    zs, zm, me = size
+    zs, zm = min(zs, E), min(zm, E)
     fs = f_smooth.reshape(E, E, E)[:zs].contiguous().cpu().numpy().ravel()
     fn = f_noise.reshape(E, E, E)[:zs].contiguous().cpu().numpy().ravel()
     mk = mask.reshape(E, E, E)[:zm].contiguous().cpu().numpy().ravel()
-    row, col = workloads.tet_mesh_csr(edge=SAMPLE_MESH_EDGE, delete_frac=0.4, seed=3, device=f_smooth.device)
+    row, col = workloads.tet_mesh_csr(edge=me, delete_frac=0.4, seed=3, device=f_smooth.device)
     return {"fs": (fs, (E, E, zs)), "fn": (fn, (E, E, zs)), "mk": (mk, (E, E, zm)),
             "mesh": (row.cpu().numpy(), col.cpu().numpy()),
             "desc": f"segment of {E}x{E}x{zs} slabs of both fields, 6-conn CC of a {E}x{E}x{zm} mask slab, "
-                    f"CC of a {SAMPLE_MESH_EDGE}^3 mesh of the same recipe ({row.numel() - 1} vertices)"}
+                    f"CC of a {me}^3 mesh of the same recipe ({row.numel() - 1} vertices)"}
 
 
 def oracle_step(sample):
@@ -473,7 +563,7 @@ def cpu_baseline(f_smooth, f_noise, mask, E):
     import oracle
 
     oracle.build()
-    sample = oracle_sample(f_smooth, f_noise, mask, E)
+    sample = oracle_sample(f_smooth, f_noise, mask, E, BASELINE_SAMPLE)
     t0 = time.perf_counter()
     verts = oracle_step(sample)
     dt = time.perf_counter() - t0
