@@ -152,7 +152,8 @@ def algorithmic_bytes(label, n, nm, nnz):
         "order.hist": 4 * n,             # read f
         "order.pass_first": 12 * n,      # read f, write (key, id)
         "order.pass": 16 * n,            # read and write (key, id)
-        "order.pass_last": 12 * n,       # read (key, id), write order
+        "order.pass_last": 16 * n,       # read (key, id), write (id, position) pairs
+        "order.scatter": 12 * n,         # read the pairs, write order
         "steepest.grid": 12 * n,         # read order, write asc + desc
         "msid.insert": 12 * n,           # read asc + desc, write slot
         "msid.lookup": 8 * n,            # read slot, write id

@@ -9,15 +9,23 @@
 //
 // One pass = one kernel.  A block takes tiles of 4096 keys from a global
 // atomic counter (so every predecessor tile is owned by a running block),
-// ranks its keys per digit with warp match-any, publishes its per-digit
-// counts to a decoupled look-back array, sums its predecessors' counts and
-// scatters.  The last pass writes order[id] = position directly.
+// ranks its keys per digit stably within each warp (ballot peers +
+// per-warp counters), publishes its per-digit counts to a decoupled
+// look-back array, sums its predecessors' counts and scatters through
+// shared memory.  The last pass files (vertex id, position) pairs into
+// buckets of consecutive ids, and a thread-block cluster scatters each
+// bucket into its distributed shared memory and writes order[id] =
+// position out as whole lines (k_pair_scatter_dsmem).
 #include <cuda_runtime.h>
+
+#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <utility>
 
 #include "sort.cuh"
+
+namespace cg = cooperative_groups;
 
 namespace msc {
 #ifdef MSC_DEBUG_BOUNDS
@@ -32,6 +40,15 @@ constexpr int kBins = 256;
 constexpr unsigned long long kFlagAgg = 1ull << 62;
 constexpr unsigned long long kFlagInc = 2ull << 62;
 constexpr uint32_t kSpinLimit = 1u << 22;
+// The last pass of the vertex order files (id, position) pairs into
+// buckets of 2^shift consecutive ids; bucket b holds exactly the ids
+// [b << shift, (b + 1) << shift) and so occupies pair slots of the same
+// range.  At most kMaxBuckets buckets; the shift is chosen so that one
+// bucket matches the id range a cluster's shared memory covers.
+constexpr int kMaxBuckets = 256;
+constexpr int kFillStride = 32;  // one 128-byte line per bucket counter: the
+                                 // tiles' reservations spread over L2 slices
+constexpr int kCounterWords = 8 + kMaxBuckets * kFillStride;  // tile counters, bucket fills
 
 __device__ __forceinline__ uint32_t float_key(float x) {
     uint32_t u = __float_as_uint(x);
@@ -239,10 +256,12 @@ struct PassArgs {
     const int32_t* vals_in;
     KeyT* keys_out;
     int32_t* vals_out;
-    int32_t* order_out;
     int64_t n;
     const int32_t* d_n;
     const uint32_t* hist;  // this pass's 256 counts
+    uint32_t* pair_pos;    // BUCKET pass: position of the id in vals_out[slot]
+    uint32_t* bucket_fill; // BUCKET pass: slots taken per bucket (stride kFillStride)
+    int bucket_shift;      // BUCKET pass: log2 of the ids per bucket
     int shift;
     unsigned long long* lookback;
     uint32_t* tile_counter;
@@ -260,19 +279,21 @@ struct PassArgs {
 
 template <typename KeyT, bool STAGE>
 constexpr size_t pass_smem_bytes() {
-    return (size_t)(kWarps * kBins + 4 * kBins + 32) * 4 +
+    return (size_t)(kWarps * kBins + 4 * kBins + 32 + 2 * kMaxBuckets) * 4 +
            (STAGE ? (size_t)kSortTile * (sizeof(KeyT) + 4) : 0);
 }
 
 // One onesweep digit pass.  FROM_F: keys come from the float field and
-// the payload is the vertex id.  TO_ORDER: write order[payload] = position
-// instead of the sorted (key, payload) arrays.
+// the payload is the vertex id.  BUCKET (last pass of the vertex order):
+// instead of the sorted (key, payload) arrays, file every (payload,
+// position) pair into the bucket of its payload's top bits (a tile
+// reserves its share of each bucket with one atomic per bucket).
 //
 // SEG: the keys are packed segments sorted independently (batched
 // instances).  Tiles never straddle two segments, the look-back stops at
 // the segment's first tile, bin starts come per segment, and positions are
 // segment-local (keys land at seg_off + position; order gets the position).
-template <typename KeyT, bool FROM_F, bool TO_ORDER, bool SEG = false>
+template <typename KeyT, bool FROM_F, bool BUCKET, bool SEG = false>
 __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a) {
     extern __shared__ __align__(16) uint8_t smem[];
     uint32_t* s_whist = reinterpret_cast<uint32_t*>(smem);  // [kWarps][256]
@@ -281,7 +302,8 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
     uint32_t* s_gbase = s_excl + kBins;                    // [256] global base of the bin
     uint32_t* s_bstart = s_gbase + kBins;                  // [256] global bin starts
     uint32_t* s_misc = s_bstart + kBins;                   // [0] tile id, [1..8] scan
-    KeyT* s_keys = reinterpret_cast<KeyT*>(s_misc + 32);
+    uint32_t* s_bucket = s_misc + 32;                      // [2][kMaxBuckets] counts, bases
+    KeyT* s_keys = reinterpret_cast<KeyT*>(s_bucket + 2 * kMaxBuckets);
     int32_t* s_vals = reinterpret_cast<int32_t*>(s_keys + kSortTile);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
@@ -395,17 +417,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
         }
         s_excl[tid] = block_scan_256(run, s_misc + 1) - run;
         __syncthreads();  // s_excl is read across threads below
-        if constexpr (TO_ORDER) {
-#pragma unroll
-            for (int k = 0; k < kItems; ++k) {
-                const uint32_t d = rk[k] >> 16;
-                if (d < 256u) {
-                    const uint32_t pos = s_gbase[d] + s_whist[warp * kBins + d] + (rk[k] & 0xffffu);
-                    MSC_GUARD((uint32_t)val[k] < (uint64_t)(SEG ? a.n : n) && pos < (uint64_t)n, a.status, -101)
-                    a.order_out[val[k]] = (int32_t)pos;
-                }
-            }
-        } else {
+        {
 #pragma unroll
             for (int k = 0; k < kItems; ++k) {
                 const uint32_t d = rk[k] >> 16;
@@ -428,13 +440,65 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
             }
             __syncthreads();
             const int cnt = (int)min((int64_t)kSortTile, n - ltile * kSortTile);
-            for (int i = tid; i < cnt; i += kThreads) {
-                const KeyT kk = s_keys[i];
-                const uint32_t d = (uint32_t)(kk >> a.shift) & 255u;
-                const uint32_t pos = s_gbase[d] + (uint32_t)i - s_excl[d];
-                MSC_GUARD(pos < (uint64_t)n, a.status, -102) {
-                    a.keys_out[seg_base + pos] = kk;
-                    a.vals_out[seg_base + pos] = s_vals[i];
+            if constexpr (BUCKET) {
+                // (id, position) pairs regrouped by bucket in shared memory, then
+                // each bucket's run written with consecutive lanes on consecutive slots
+                static_assert(kMaxBuckets == kThreads, "one bucket per thread");
+                uint32_t* s_bstart2 = s_bucket;              // counts, then tile-local bucket starts
+                uint32_t* s_bbase = s_bucket + kMaxBuckets;  // first global slot of the tile's run
+                s_bstart2[tid] = 0;
+                __syncthreads();
+                uint32_t pid[kItems], ppos[kItems], prank[kItems / 2];  // two 16-bit ranks per word
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
+                    const int i = tid + k * kThreads;
+                    if (k % 2 == 0) prank[k / 2] = 0;
+                    if (i < cnt) {
+                        pid[k] = (uint32_t)s_vals[i];
+                        const uint32_t d = (uint32_t)(s_keys[i] >> a.shift) & 255u;
+                        ppos[k] = s_gbase[d] + (uint32_t)i - s_excl[d];
+                        prank[k / 2] |= atomicAdd(&s_bstart2[pid[k] >> a.bucket_shift], 1u) << (16 * (k % 2));
+                    }
+                }
+                __syncthreads();
+                {
+                    const uint32_t c = s_bstart2[tid];
+                    const uint32_t start = block_scan_256(c, s_misc + 1) - c;
+                    s_bbase[tid] = c ? ((uint32_t)tid << a.bucket_shift) +
+                                           atomicAdd(&a.bucket_fill[tid * kFillStride], c)
+                                     : 0u;
+                    s_bstart2[tid] = start;
+                }
+                __syncthreads();
+#pragma unroll
+                for (int k = 0; k < kItems; ++k) {
+                    const int i = tid + k * kThreads;
+                    if (i < cnt) {
+                        const uint32_t j = s_bstart2[pid[k] >> a.bucket_shift] + ((prank[k / 2] >> (16 * (k % 2))) & 0xffffu);
+                        s_keys[j] = (KeyT)ppos[k];
+                        s_vals[j] = (int32_t)pid[k];
+                    }
+                }
+                __syncthreads();
+                for (int i = tid; i < cnt; i += kThreads) {
+                    const uint32_t id = (uint32_t)s_vals[i];
+                    const uint32_t b = id >> a.bucket_shift;
+                    const uint32_t slot = s_bbase[b] + ((uint32_t)i - s_bstart2[b]);
+                    const uint32_t pos = (uint32_t)s_keys[i];
+                    MSC_GUARD(slot < (uint64_t)a.n && pos < (uint64_t)n, a.status, -102) {
+                        a.vals_out[slot] = (int32_t)id;
+                        a.pair_pos[slot] = pos;
+                    }
+                }
+            } else {
+                for (int i = tid; i < cnt; i += kThreads) {
+                    const KeyT kk = s_keys[i];
+                    const uint32_t d = (uint32_t)(kk >> a.shift) & 255u;
+                    const uint32_t pos = s_gbase[d] + (uint32_t)i - s_excl[d];
+                    MSC_GUARD(pos < (uint64_t)n, a.status, -102) {
+                        a.keys_out[seg_base + pos] = kk;
+                        a.vals_out[seg_base + pos] = s_vals[i];
+                    }
                 }
             }
         }
@@ -442,10 +506,203 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
     }
 }
 
-template <typename KeyT, bool FROM_F, bool TO_ORDER, bool SEG = false>
+// order[ids[slot]] = pos[slot] for every filed pair (fallback when no
+// cluster can be launched): scattered 4-byte writes straight to memory.
+__global__ void __launch_bounds__(256) k_pair_scatter(const int32_t* __restrict__ ids,
+                                                      const uint32_t* __restrict__ pos, int64_t n,
+                                                      int32_t* __restrict__ order, int32_t* status) {
+    constexpr int kPer = kSortTile / 256;
+    for (int64_t t = blockIdx.x; t * kSortTile < n; t += gridDim.x) {
+        int32_t id[kPer];
+        uint32_t ps[kPer];
+#pragma unroll
+        for (int j = 0; j < kPer; ++j) {
+            const int64_t i = t * kSortTile + j * 256 + threadIdx.x;
+            id[j] = i < n ? __ldcs(ids + i) : -1;
+            ps[j] = i < n ? __ldcs(pos + i) : 0u;
+        }
+#pragma unroll
+        for (int j = 0; j < kPer; ++j)
+            if (id[j] >= 0) {
+                MSC_GUARD((int64_t)id[j] < n, status, -104)
+                order[id[j]] = (int32_t)ps[j];
+            }
+    }
+}
+
+// The same through distributed shared memory.  A cluster of C CTAs holds
+// C * 2^15 consecutive entries of the order array in shared memory (128 KiB
+// per CTA).  For each bucket (or part of a bucket that the cluster
+// covers) its CTAs stream the bucket's pairs, store every position into
+// the shared-memory slice of the CTA that owns the id (a remote store
+// within the cluster), synchronise the cluster, and write their slices out
+// as whole lines.  DRAM sees each pair read once and each order entry
+// written once.
+constexpr int kSliceLog2 = 15;
+constexpr int kSliceIds = 1 << kSliceLog2;
+constexpr int kScatterThreads = 1024;
+
+template <int C>
+__global__ void __launch_bounds__(kScatterThreads, 1) k_pair_scatter_dsmem(const int32_t* __restrict__ ids,
+                                                                          const uint32_t* __restrict__ pos,
+                                                                          int64_t n, int bucket_shift,
+                                                                          int32_t* __restrict__ order,
+                                                                          int32_t* status) {
+    extern __shared__ __align__(16) int32_t slice[];  // kSliceIds
+    cg::cluster_group cl = cg::this_cluster();
+    const int rank = (int)cl.block_rank();
+    const int64_t ncl = gridDim.x / C, cid = blockIdx.x / C;
+    const int64_t W = int64_t(1) << bucket_shift;
+    constexpr int64_t kCover = (int64_t)C * kSliceIds;
+    const int64_t subs = W > kCover ? W / kCover : 1;  // W and kCover are powers of two
+    const int64_t nb = (n + W - 1) >> bucket_shift;
+    for (int64_t job = cid; job < nb * subs; job += ncl) {
+        const int64_t b = job / subs, sr = job - b * subs;
+        const int64_t s0 = b * W, s1 = min(n, s0 + W);  // the bucket's slots = its ids
+        const int64_t lo = s0 + sr * kCover;            // first id of this part
+        // 16-byte loads of 4 consecutive pairs, kUnroll groups per thread in
+        // flight (loads first, then the remote stores); a ragged end of the
+        // bucket goes pair by pair
+        constexpr int kUnroll = 2;
+        constexpr int64_t kStep = (int64_t)C * kScatterThreads;  // groups of 4 per sweep
+        const int64_t groups = (s1 - s0) >> 2;
+        auto put = [&](int32_t id, uint32_t p) {
+            const int64_t off = (int64_t)id - lo;
+            if (off >= 0 && off < kCover)
+                *cl.map_shared_rank(slice + (off & (kSliceIds - 1)), (unsigned)(off >> kSliceLog2)) = (int32_t)p;
+            else if (subs == 1)
+                record_error(status, MSC_ERR_INTERNAL);  // an id outside its bucket
+        };
+        for (int64_t g0 = (int64_t)rank * kScatterThreads + threadIdx.x; g0 < groups; g0 += kUnroll * kStep) {
+            int4 id[kUnroll];
+            uint4 p[kUnroll];
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                const int64_t g = g0 + u * kStep;
+                if (g < groups) {
+                    id[u] = __ldcs(reinterpret_cast<const int4*>(ids + s0) + g);
+                    p[u] = __ldcs(reinterpret_cast<const uint4*>(pos + s0) + g);
+                } else {
+                    id[u] = make_int4(-1, -1, -1, -1);
+                }
+            }
+#pragma unroll
+            for (int u = 0; u < kUnroll; ++u) {
+                if (id[u].x < 0) continue;
+                put(id[u].x, p[u].x);
+                put(id[u].y, p[u].y);
+                put(id[u].z, p[u].z);
+                put(id[u].w, p[u].w);
+            }
+        }
+        for (int64_t sl = s0 + groups * 4 + (int64_t)rank * kScatterThreads + threadIdx.x; sl < s1; sl += kStep)
+            put(__ldcs(ids + sl), __ldcs(pos + sl));
+        cl.sync();  // every remote store has landed
+        const int64_t m0 = lo + (int64_t)rank * kSliceIds;  // a multiple of 2^15
+        const int64_t m1 = min(m0 + kSliceIds, s1);
+        const int64_t full = m1 > m0 ? (m1 - m0) >> 2 : 0;
+        for (int64_t i = threadIdx.x; i < full; i += kScatterThreads)
+            reinterpret_cast<int4*>(order + m0)[i] = reinterpret_cast<const int4*>(slice)[i];
+        for (int64_t i = full * 4 + threadIdx.x; m0 + i < m1; i += kScatterThreads) order[m0 + i] = slice[i];
+        cl.sync();  // slices are free for the next part
+    }
+}
+
+struct ScatterPlan {
+    int cluster = 0;  // 16 or 8 CTAs; 0: no cluster fits, plain scatter
+    int clusters = 0; // clusters resident at once
+    int shift = 0;    // log2 ids per bucket
+};
+
+template <int C>
+int dsmem_clusters() {
+    auto kern = k_pair_scatter_dsmem<C>;
+    const int smem = kSliceIds * 4;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
+    if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
+        return 0;
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(C);
+    cfg.blockDim = dim3(kScatterThreads);
+    cfg.dynamicSmemBytes = smem;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = C;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int num = 0;
+    if (cudaOccupancyMaxActiveClusters(&num, kern, &cfg) != cudaSuccess) {
+        cudaGetLastError();
+        return 0;
+    }
+    return num;
+}
+
+// Cluster shape and bucket width for n ids (cached per device).
+ScatterPlan scatter_plan(int64_t n) {
+    static ScatterPlan per_dev[64];
+    static bool done[64] = {};
+    const int dev = current_device().id & 63;
+    if (!done[dev]) {
+        ScatterPlan p;
+        if ((p.clusters = dsmem_clusters<16>()) > 0) p.cluster = 16;
+        else if ((p.clusters = dsmem_clusters<8>()) > 0) p.cluster = 8;
+        per_dev[dev] = p;
+        done[dev] = true;
+    }
+    ScatterPlan p = per_dev[dev];
+    const int cover_log2 = p.cluster == 16 ? kSliceLog2 + 4 : kSliceLog2 + 3;
+    p.shift = std::max(cover_log2, ceil_log2(ceil_div(std::max<int64_t>(n, 1), kMaxBuckets)));
+    return p;
+}
+
+int launch_pair_scatter(const ScatterPlan& p, const int32_t* ids, const uint32_t* pos, int64_t n, int32_t* order,
+                        int32_t* status, cudaStream_t s) {
+    if (p.cluster == 0) {
+        const int64_t tiles = ceil_div(n, kSortTile);
+        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)current_device().sms * 8));
+        {
+            TraceScope ts_("order.scatter", s);
+            k_pair_scatter<<<grid, 256, 0, s>>>(ids, pos, n, order, status);
+        }
+        MSC_LAUNCHED();
+        return MSC_OK;
+    }
+    const int64_t W = int64_t(1) << p.shift;
+    const int64_t cover = (int64_t)p.cluster << kSliceLog2;
+    const int64_t jobs = ceil_div(n, W) * std::max<int64_t>(1, W / cover);
+    const int64_t ncl = std::max<int64_t>(1, std::min<int64_t>(jobs, p.clusters));
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3((unsigned)(ncl * p.cluster));
+    cfg.blockDim = dim3(kScatterThreads);
+    cfg.dynamicSmemBytes = kSliceIds * 4;
+    cfg.stream = s;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = p.cluster;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    cudaError_t e;
+    {
+        TraceScope ts_("order.scatter", s);
+        e = p.cluster == 16 ? cudaLaunchKernelEx(&cfg, k_pair_scatter_dsmem<16>, ids, pos, n, p.shift, order, status)
+                            : cudaLaunchKernelEx(&cfg, k_pair_scatter_dsmem<8>, ids, pos, n, p.shift, order, status);
+    }
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        return MSC_ERR_CUDA;
+    }
+    return MSC_OK;
+}
+
+template <typename KeyT, bool FROM_F, bool BUCKET, bool SEG = false>
 int launch_pass(const PassArgs<KeyT>& a, int64_t max_n, cudaStream_t s, const char* label) {
-    constexpr size_t smem = pass_smem_bytes<KeyT, !TO_ORDER>();
-    auto kern = k_onesweep<KeyT, FROM_F, TO_ORDER, SEG>;
+    constexpr size_t smem = pass_smem_bytes<KeyT, true>();
+    auto kern = k_onesweep<KeyT, FROM_F, BUCKET, SEG>;
     static int configured_dev = -1;  // the attribute is set once per device
     if (configured_dev != current_device().id) {
         MSC_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -466,13 +723,13 @@ int launch_pass(const PassArgs<KeyT>& a, int64_t max_n, cudaStream_t s, const ch
 }  // namespace
 
 void size_sort_scratch(Sizer& s, int64_t n) {
-    s.take<uint32_t>(8 * kBins + 8);
+    s.take<uint32_t>(8 * kBins + kCounterWords);
     s.take<unsigned long long>((size_t)std::max<int64_t>(1, ceil_div(n, kSortTile)) * kBins);
 }
 
 SortScratch carve_sort_scratch(Carver& c, int64_t n) {
     SortScratch sc;
-    sc.hist = c.take<uint32_t>(8 * kBins + 8);
+    sc.hist = c.take<uint32_t>(8 * kBins + kCounterWords);
     sc.tile_counters = sc.hist + 8 * kBins;
     sc.max_tiles = std::max<int64_t>(1, ceil_div(n, kSortTile));
     sc.lookback = c.take<unsigned long long>((size_t)sc.max_tiles * kBins);
@@ -480,7 +737,7 @@ SortScratch carve_sort_scratch(Carver& c, int64_t n) {
 }
 
 static int clear_scratch(const SortScratch& sc, int64_t n, cudaStream_t s) {
-    MSC_TRY(cudaMemsetAsync(sc.hist, 0, (8 * kBins + 8) * sizeof(uint32_t), s));
+    MSC_TRY(cudaMemsetAsync(sc.hist, 0, (8 * kBins + kCounterWords) * sizeof(uint32_t), s));
     const int64_t tiles = std::max<int64_t>(1, ceil_div(n, kSortTile));
     MSC_TRY(cudaMemsetAsync(sc.lookback, 0, (size_t)tiles * kBins * sizeof(unsigned long long), s));
     return MSC_OK;
@@ -550,28 +807,33 @@ int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_
         std::swap(kin, kout);
         std::swap(iin, iout);
     }
-    // pass 3: a -> order
+    // pass 3: a -> (id, position) pairs by id bucket in the free buffers,
+    // then order[id] = position
     a.keys_in = kin;
     a.vals_in = iin;
     a.keys_out = nullptr;
-    a.vals_out = nullptr;
-    a.order_out = order;
+    a.vals_out = iout;
+    a.pair_pos = kout;
+    a.bucket_fill = sc.tile_counters + 8;
+    const ScatterPlan plan = scatter_plan(n);
+    a.bucket_shift = plan.shift;
     a.hist = sc.hist + 3 * kBins;
     a.shift = 24;
     a.tile_counter = sc.tile_counters + 3;
     a.epoch = 4;
-    return launch_pass<uint32_t, false, true>(a, n, s, "order.pass_last");
+    if ((r = launch_pass<uint32_t, false, true>(a, n, s, "order.pass_last"))) return r;
+    return launch_pair_scatter(plan, iout, kout, n, order, status, s);
 }
 
 void size_seg_sort_scratch(Sizer& s, int count, int64_t tiles) {
-    s.take<uint32_t>((size_t)count * kSegPasses * kBins + 8);
+    s.take<uint32_t>((size_t)count * kSegPasses * kBins + kCounterWords);
     s.take<unsigned long long>((size_t)std::max<int64_t>(1, tiles) * kBins);
 }
 
 SortScratch carve_seg_sort_scratch(Carver& c, int count, int64_t tiles) {
     SortScratch sc;
     const size_t hist_words = (size_t)count * kSegPasses * kBins;
-    sc.hist = c.take<uint32_t>(hist_words + 8);
+    sc.hist = c.take<uint32_t>(hist_words + kCounterWords);
     sc.tile_counters = sc.hist + hist_words;
     sc.max_tiles = std::max<int64_t>(1, tiles);
     sc.lookback = c.take<unsigned long long>((size_t)sc.max_tiles * kBins);
@@ -583,7 +845,7 @@ int run_order_seg(const float* f, const SegTable& t, int32_t* order, uint32_t* k
                   cudaStream_t s) {
     if (t.tiles <= 0) return MSC_OK;
     const size_t hist_words = (size_t)t.count * kSegPasses * kBins;
-    MSC_TRY(cudaMemsetAsync(sc.hist, 0, (hist_words + 8) * sizeof(uint32_t), s));
+    MSC_TRY(cudaMemsetAsync(sc.hist, 0, (hist_words + kCounterWords) * sizeof(uint32_t), s));
     MSC_TRY(cudaMemsetAsync(sc.lookback, 0, (size_t)t.tiles * kBins * sizeof(unsigned long long), s));
     int r = configure_hist();
     if (r) return r;
@@ -636,13 +898,17 @@ int run_order_seg(const float* f, const SegTable& t, int32_t* order, uint32_t* k
     a.keys_in = kin;
     a.vals_in = iin;
     a.keys_out = nullptr;
-    a.vals_out = nullptr;
-    a.order_out = order;
+    a.vals_out = iout;
+    a.pair_pos = kout;
+    a.bucket_fill = sc.tile_counters + 8;
+    const ScatterPlan plan = scatter_plan(t.total);
+    a.bucket_shift = plan.shift;
     a.hist = sc.hist + 3 * kBins;
     a.shift = 24;
     a.tile_counter = sc.tile_counters + 3;
     a.epoch = 4;
-    return launch_pass<uint32_t, false, true, true>(a, t.total, s, "order.pass_last");
+    if ((r = launch_pass<uint32_t, false, true, true>(a, t.total, s, "order.pass_last"))) return r;
+    return launch_pair_scatter(plan, iout, kout, t.total, order, status, s);
 }
 
 int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* keys_alt,

@@ -1,0 +1,148 @@
+"""The hot path at the benchmarked sizes, in the launch configuration the
+benchmark times (the C ABI with one workspace per call).
+
+At these sizes the oracle cannot redo everything, so each output is checked
+in two ways: (1) sampled vertices against the oracle's per-vertex functions
+(order by counting, steepest neighbour, the walk to both extrema, the
+component by BFS), and (2) properties that together pin the result
+completely at any size:
+
+* order: a permutation with (f, id) non-decreasing along the inverse;
+* labels: every label is a fixed point of the pointers, the labels are the
+  extrema, the cell ids rank the distinct (asc, desc) pairs;
+* components: -1 exactly off the mask, label[v] <= v, label[label[v]] =
+  label[v], and equal labels across every masked 6-neighbour pair -- which
+  makes the label the smallest id of the component.
+"""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def m():
+    import paper_2409_03771_gb300 as msc
+    from paper_2409_03771_gb300 import _build
+
+    _build.build()
+    msc.load()
+    return msc
+
+
+def check_order_properties(f, order):
+    n = f.numel()
+    o = order.long()
+    assert int(o.min()) == 0 and int(o.max()) == n - 1
+    assert bool((torch.bincount(o, minlength=n) == 1).all()), "order is not a permutation"
+    inv = torch.empty(n, dtype=torch.long, device=f.device)
+    inv[o] = torch.arange(n, device=f.device)
+    fs = f[inv]
+    assert bool((fs[1:] >= fs[:-1]).all()), "values decrease along the order"
+    tie = fs[1:] == fs[:-1]
+    assert bool((inv[1:][tie] > inv[:-1][tie]).all()), "ties not broken by id"
+
+
+@pytest.mark.parametrize("n", [3_000_017, (1 << 27) + 12345])
+def test_order_large_properties(m, n):
+    g = torch.Generator(device="cuda").manual_seed(n)
+    # heavy ties (2^16 distinct values) plus signed zeros
+    f = (torch.randint(-(1 << 15), 1 << 15, (n,), device="cuda", generator=g).float() / 64.0)
+    f[::7] = -0.0
+    check_order_properties(f, m.order(f))
+
+
+def is_extremum(order, dims, larger):
+    """True at v when every in-grid Freudenthal neighbour of v has a smaller
+    (larger=True) or larger (larger=False) order than v."""
+    nx, ny, nz = dims
+    o = order.reshape(nz, ny, nx)
+    ok = torch.ones_like(o, dtype=torch.bool)
+    for dx, dy, dz in [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)]:
+        for sgn in (1, -1):
+            ax, ay, az = sgn * dx, sgn * dy, sgn * dz
+            here = (slice(max(0, -az), nz - max(0, az)), slice(max(0, -ay), ny - max(0, ay)),
+                    slice(max(0, -ax), nx - max(0, ax)))
+            there = (slice(max(0, az), nz - max(0, -az)), slice(max(0, ay), ny - max(0, -ay)),
+                     slice(max(0, ax), nx - max(0, -ax)))
+            sub = ok[here]  # a view: updated in place
+            sub &= (o[there] < o[here]) if larger else (o[there] > o[here])
+    return ok.reshape(-1)
+
+
+@pytest.mark.parametrize("kind", ["smooth", "noise"])
+def test_segment_512_sampled_and_properties(m, oracle_mod, kind):
+    E = 512
+    dims = (E, E, E)
+    f = (workloads.field_smooth(edge=E, seed=1, device="cuda") if kind == "smooth"
+         else workloads.field_noise(edge=E, seed=1, device="cuda")).reshape(-1)
+    n = f.numel()
+    ws = torch.empty(m.msc_workspace_bytes(m.OP_SEGMENT, n), dtype=torch.uint8, device="cuda")
+    order, asc, desc, ms, cells = m.segment(f, dims, ws=ws)
+    check_order_properties(f, order)
+    # labels are extrema and fixed points; every extremum labels itself
+    is_max = is_extremum(order, dims, larger=True)
+    is_min = is_extremum(order, dims, larger=False)
+    d, a = desc.long(), asc.long()
+    assert bool((desc[d] == desc).all()) and bool((asc[a] == asc).all())
+    assert bool(is_max[d].all()) and bool(is_min[a].all())
+    ids = torch.arange(n, device="cuda")
+    assert bool((desc[is_max] == ids[is_max]).all()) and bool((asc[is_min] == ids[is_min]).all())
+    # cell ids rank the distinct pairs
+    key = a * n + d
+    uniq, inv = torch.unique(key, return_inverse=True)
+    assert cells == uniq.numel()
+    assert torch.equal(ms.long(), inv)
+    # sampled vertices against the oracle
+    fh = f.cpu().numpy()
+    rng = np.random.default_rng(7)
+    asc_ptr, desc_ptr = m.steepest_grid(order, dims)
+    for v in rng.integers(0, n, 48):
+        v = int(v)
+        assert oracle_mod.labels_at(fh, dims, v) == (int(asc[v]), int(desc[v])), v
+        assert oracle_mod.steepest_at(fh, dims, v) == (int(asc_ptr[v]), int(desc_ptr[v])), v
+    for v in rng.integers(0, n, 3):
+        assert oracle_mod.order_at(fh, int(v)) == int(order[int(v)])
+
+
+def test_cc_mask_1024_properties_and_samples(m, oracle_mod):
+    E = 1024
+    dims = (E, E, E)
+    mask = workloads.mask_blobs(edge=E, seed=2, device="cuda").reshape(-1)
+    lab = m.cc_mask(mask, dims, 6)
+    n = mask.numel()
+    on = mask != 0
+    assert bool(((lab == -1) == ~on).all())
+    l = lab.long()
+    ids = torch.arange(n, device="cuda")
+    assert bool((l[on] <= ids[on]).all())
+    assert bool((lab[l[on]] == lab[on]).all())
+    L = lab.reshape(E, E, E)
+    M = on.reshape(E, E, E)
+    for dim in range(3):
+        a = [slice(None)] * 3
+        b = [slice(None)] * 3
+        a[dim] = slice(0, E - 1)
+        b[dim] = slice(1, E)
+        both = M[tuple(a)] & M[tuple(b)]
+        assert bool((L[tuple(a)][both] == L[tuple(b)][both]).all()), f"label changes across axis {dim}"
+    # the three smallest components against BFS from one of their vertices
+    sizes = torch.bincount(l[on], minlength=n)
+    roots = torch.nonzero(sizes).reshape(-1)
+    small = roots[torch.argsort(sizes[roots])[:3]].cpu().numpy()
+    del L, M, l, ids, sizes, roots
+    mh = mask.cpu().numpy()
+    rng = np.random.default_rng(3)
+    for root in small:
+        members = torch.nonzero(lab == int(root)).reshape(-1)
+        v = int(members[int(rng.integers(0, members.numel()))])
+        assert oracle_mod.cc_grid_at(mh, dims, 6, v) == (int(root), members.numel())  # (min id, size)
+
+
+def test_cc_mesh_256_full_oracle(m, oracle_mod):
+    row, col = workloads.tet_mesh_csr(edge=256, delete_frac=0.4, seed=3, device="cuda")
+    lab = m.cc_mesh(row, col)
+    np.testing.assert_array_equal(lab.cpu().numpy(), oracle_mod.cc_csr(row.cpu().numpy(), col.cpu().numpy()))
