@@ -55,13 +55,18 @@ constexpr int kChunkV = kThreads * kPerThread;
 // hop always lands on a strict ancestor, so landing on the vertex itself
 // can only happen on a pointer cycle (in-place jumping can collapse a
 // cycle into such a self-loop, which would otherwise look converged).
+//
+// CHECKED = false (pointers made by the stencil kernels: in range and
+// acyclic by construction, since order strictly increases along them)
+// drops the per-hop range and cycle tests.
+template <bool CHECKED>
 __device__ __forceinline__ uint32_t jump_group(const int32_t* p, int32_t n, const int32_t (&vid)[kPerThread],
                                                int32_t (&d)[kPerThread], uint32_t valid, int32_t* status) {
     uint32_t live = 0, moved = 0;
 #pragma unroll
     for (int j = 0; j < kPerThread; ++j) {
         if (!(valid >> j & 1u) || d[j] < 0) continue;
-        if ((uint32_t)d[j] >= (uint32_t)n) {
+        if (CHECKED && (uint32_t)d[j] >= (uint32_t)n) {
             record_error(status, MSC_ERR_ARG);
             continue;
         }
@@ -78,10 +83,10 @@ __device__ __forceinline__ uint32_t jump_group(const int32_t* p, int32_t n, cons
             const int32_t u = d[j];
             if (w[j] == u) {
                 live &= ~(1u << j);  // u is a root: done
-            } else if ((uint32_t)w[j] >= (uint32_t)n) {
+            } else if (CHECKED && (uint32_t)w[j] >= (uint32_t)n) {
                 record_error(status, MSC_ERR_ARG);  // out of range or inactive target
                 live &= ~(1u << j);
-            } else if (w[j] == vid[j]) {
+            } else if (CHECKED && w[j] == vid[j]) {
                 record_error(status, MSC_ERR_NOT_CONVERGED);
                 live &= ~(1u << j);
             } else {
@@ -93,6 +98,7 @@ __device__ __forceinline__ uint32_t jump_group(const int32_t* p, int32_t n, cons
     return moved;
 }
 
+template <bool CHECKED>
 __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, int build_shift,
                                                    int32_t* status) {
     const JumpArray A = blockIdx.y ? pr.a[1] : pr.a[0];
@@ -144,7 +150,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, 
 #pragma unroll
             for (int j = 0; j < kPerThread; ++j) d[j] = (valid >> j & 1u) ? p[vid[j]] : -1;
         }
-        ch = jump_group(p, n, vid, d, valid, status);
+        ch = jump_group<CHECKED>(p, n, vid, d, valid, status);
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j)
             if (ch >> j & 1u) p[vid[j]] = d[j];
@@ -230,15 +236,16 @@ int run_compress(int32_t* const* ptrs, int count, int32_t n, const CompressScrat
         pr.a[i].list1 = pr.a[i].list0 + sc.list_cap;
     }
     const int build_shift = std::max(1, std::min(tune.build_shift, 30));
+    auto kern = tune.trusted ? k_jump<false> : k_jump<true>;
     int occ = 1;
-    MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k_jump, kThreads, 0));
+    MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
     const int64_t chunks = ceil_div(n, kChunkV);
     const int gx = (int)std::max<int64_t>(1, std::min<int64_t>(chunks, (int64_t)current_device().sms * std::max(occ, 1)));
     const int steps = compress_steps(n);
     for (int st = 0; st < steps; ++st) {
         {
             TraceScope ts_("compress.jump", s);
-            k_jump<<<dim3(gx, count), kThreads, 0, s>>>(pr, st, build_shift, status);
+            kern<<<dim3(gx, count), kThreads, 0, s>>>(pr, st, build_shift, status);
         }
         MSC_LAUNCHED();
     }

@@ -15,7 +15,8 @@ struct JumpCtl {
 };
 
 struct CompressTune {
-    int build_shift = 3;  // build the active list once <= n >> build_shift changed
+    int build_shift = 3;   // build the active list once <= n >> build_shift changed
+    bool trusted = false;  // pointers from the stencil kernels: skip range / cycle tests
 };
 
 // Sweeps launched for n vertices: ceil(log4 n) + 2 (enough for any forest

@@ -223,7 +223,9 @@ int msc_segment(const float* f, msc_grid g, int32_t* order, int32_t* asc, int32_
         st.used = stage_off;
         CompressScratch sc = carve_compress_scratch(st, n, 2);
         int32_t* arr[2] = {asc, desc};
-        r = run_compress(arr, 2, (int32_t)n, sc, d_status, s);
+        CompressTune tune;
+        tune.trusted = true;  // made by the stencil above: in range, acyclic
+        r = run_compress(arr, 2, (int32_t)n, sc, d_status, s, tune);
         if (r) return r;
     }
     // 4. dense Morse-Smale ids
