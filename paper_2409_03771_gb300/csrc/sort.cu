@@ -328,26 +328,34 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
             ltile = tile - a.seg_tile0[seg];
             s_bstart[tid] = a.hist[(int64_t)seg * a.seg_stride + tid];  // read by this thread only
         }
-        const int64_t base = ltile * kSortTile + warp * (kItems * 32);
+        // tile-local 32-bit indices from here on: the tile's keys are
+        // [tbase, tbase + cnt) of the packed arrays
+        const int64_t tbase = seg_base + ltile * kSortTile;
+        const int cnt = (int)min((int64_t)kSortTile, n - ltile * kSortTile);
+        const int wbase = warp * (kItems * 32) + lane;
 
         KeyT key[kItems];
         int32_t val[kItems];
         uint32_t rk[kItems];  // (digit << 16) | rank among the warp's equal digits
+        {
+            const KeyT* kin = FROM_F ? nullptr : a.keys_in + tbase;
+            const int32_t* vin = FROM_F ? nullptr : a.vals_in + tbase;
+            const float* fin = FROM_F ? a.f_in + tbase : nullptr;
 #pragma unroll
-        for (int k = 0; k < kItems; ++k) {
-            const int64_t idx = base + k * 32 + lane;
-            if (idx < n) {
-                const int64_t gidx = seg_base + idx;
-                if constexpr (FROM_F) {
-                    key[k] = (KeyT)float_key(a.f_in[gidx]);
-                    val[k] = (int32_t)gidx;
+            for (int k = 0; k < kItems; ++k) {
+                const int li = wbase + k * 32;
+                if (li < cnt) {
+                    if constexpr (FROM_F) {
+                        key[k] = (KeyT)float_key(fin[li]);
+                        val[k] = (int32_t)tbase + li;
+                    } else {
+                        key[k] = kin[li];
+                        val[k] = vin[li];
+                    }
                 } else {
-                    key[k] = a.keys_in[gidx];
-                    val[k] = a.vals_in[gidx];
+                    key[k] = 0;
+                    val[k] = -1;
                 }
-            } else {
-                key[k] = 0;
-                val[k] = -1;
             }
         }
         uint32_t* wh = s_whist + warp * kBins;
@@ -356,7 +364,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
         for (int k = 0; k < kItems; ++k) {
             // stable rank among the warp's equal digits: earlier iterations
             // (warp counter) + lower lanes of this iteration (ballot peers)
-            const bool valid = base + k * 32 + lane < n;
+            const bool valid = wbase + k * 32 < cnt;
             const uint32_t d = (uint32_t)(key[k] >> a.shift) & 255u;
             const uint32_t peers = digit_peers(d, valid);
             const uint32_t lower = __popc(peers & lt);
@@ -371,7 +379,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
             uint32_t sum = 0;
             for (int i = lane; i < kBins; i += 32) sum += wh[i];
             for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-            const int64_t wv = min((int64_t)(kItems * 32), max((int64_t)0, n - base));
+            const int64_t wv = min(kItems * 32, max(0, cnt - warp * kItems * 32));
             if (lane == 0 && sum != (uint32_t)wv && atomicCAS(&g_sort_dbg[14], 0u, 1u) == 0u) {
                 g_sort_dbg[15] = (uint32_t)((tile & 0xffffu) << 16 | (warp << 12) | (sum & 0xfffu));
             }
@@ -439,7 +447,6 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
                 }
             }
             __syncthreads();
-            const int cnt = (int)min((int64_t)kSortTile, n - ltile * kSortTile);
             if constexpr (BUCKET) {
                 // (id, position) pairs regrouped by bucket in shared memory, then
                 // each bucket's run written with consecutive lanes on consecutive slots
@@ -491,13 +498,15 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
                     }
                 }
             } else {
+                KeyT* kout = a.keys_out + seg_base;
+                int32_t* vout = a.vals_out + seg_base;
                 for (int i = tid; i < cnt; i += kThreads) {
                     const KeyT kk = s_keys[i];
                     const uint32_t d = (uint32_t)(kk >> a.shift) & 255u;
                     const uint32_t pos = s_gbase[d] + (uint32_t)i - s_excl[d];
                     MSC_GUARD(pos < (uint64_t)n, a.status, -102) {
-                        a.keys_out[seg_base + pos] = kk;
-                        a.vals_out[seg_base + pos] = s_vals[i];
+                        kout[pos] = kk;
+                        vout[pos] = s_vals[i];
                     }
                 }
             }
