@@ -39,6 +39,7 @@ struct JumpArray {
 struct JumpPair {
     JumpArray a[2];
     int32_t n;
+    uint32_t* roots;  // optional: roots[i] += #vertices of array i that point at themselves
 };
 
 constexpr int kHops = 3;  // pointer hops followed per vertex and sweep
@@ -117,7 +118,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int64_t total = from_list ? (int64_t)prev : (int64_t)n;
     const int64_t nchunks = (total + kChunkV - 1) / kChunkV;
-    uint32_t changed_total = 0;
+    uint32_t changed_total = 0, roots_seen = 0;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
         int32_t vid[kPerThread], d[kPerThread];
         uint32_t valid = 0, ch;
@@ -149,6 +150,12 @@ __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, 
             }
 #pragma unroll
             for (int j = 0; j < kPerThread; ++j) d[j] = (valid >> j & 1u) ? p[vid[j]] : -1;
+        }
+        if (step == 0 && pr.roots) {  // the first sweep sees every pointer: count the roots
+            uint32_t r = 0;
+#pragma unroll
+            for (int j = 0; j < kPerThread; ++j) r += (valid >> j & 1u) && d[j] == vid[j];
+            roots_seen += r;
         }
         ch = jump_group<CHECKED>(p, n, vid, d, valid, status);
 #pragma unroll
@@ -191,6 +198,11 @@ __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, 
         for (int o = 16; o > 0; o >>= 1) changed_total += __shfl_xor_sync(0xffffffffu, changed_total, o);
         if (lane == 0 && changed_total) atomicAdd(&A.ctl->cnt[step], changed_total);
     }
+    if (step == 0 && pr.roots) {
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) roots_seen += __shfl_xor_sync(0xffffffffu, roots_seen, o);
+        if (lane == 0 && roots_seen) atomicAdd(&pr.roots[blockIdx.y], roots_seen);
+    }
 }
 
 __global__ void k_jump_finish(const JumpPair pr, int count, int last, int32_t* status) {
@@ -229,6 +241,7 @@ int run_compress(int32_t* const* ptrs, int count, int32_t n, const CompressScrat
     MSC_TRY(cudaMemsetAsync(sc.ctl, 0, sizeof(JumpCtl) * count, s));
     JumpPair pr{};
     pr.n = n;
+    pr.roots = tune.roots;
     for (int i = 0; i < count; ++i) {
         pr.a[i].p = ptrs[i];
         pr.a[i].ctl = sc.ctl + i;

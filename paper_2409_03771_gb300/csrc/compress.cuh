@@ -17,6 +17,7 @@ struct JumpCtl {
 struct CompressTune {
     int build_shift = 3;   // build the active list once <= n >> build_shift changed
     bool trusted = false;  // pointers from the stencil kernels: skip range / cycle tests
+    uint32_t* roots = nullptr;  // roots[i] += #self-pointers of array i (first sweep)
 };
 
 // Sweeps launched for n vertices: ceil(log4 n) + 2 (enough for any forest

@@ -214,8 +214,8 @@ int msc_segment(const float* f, msc_grid g, int32_t* order, int32_t* asc, int32_
                           reinterpret_cast<uint32_t*>(ms), ib, sc, d_status, s);
         if (r) return r;
     }
-    // 2. steepest pointers (+ extrema counts in common[0..1])
-    int r = run_steepest_grid(order, g, asc, desc, common, d_status, s);
+    // 2. steepest pointers (the extrema are counted by the first jump sweep)
+    int r = run_steepest_grid(order, g, asc, desc, nullptr, d_status, s);
     if (r) return r;
     // 3. pointer jumping on both arrays
     {
@@ -225,6 +225,7 @@ int msc_segment(const float* f, msc_grid g, int32_t* order, int32_t* asc, int32_
         int32_t* arr[2] = {asc, desc};
         CompressTune tune;
         tune.trusted = true;  // made by the stencil above: in range, acyclic
+        tune.roots = common;  // common[0] = #minima (asc roots), common[1] = #maxima
         r = run_compress(arr, 2, (int32_t)n, sc, d_status, s, tune);
         if (r) return r;
     }

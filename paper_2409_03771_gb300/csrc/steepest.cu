@@ -29,7 +29,7 @@ constexpr uint32_t kWaitLimit = 1u << 22;
 
 // A tile of TX x TY x TZ vertices and its shared-memory box (4 halo cells
 // in x, keeping 16-byte alignment, 1 in y and z).  A thread takes four
-// consecutive x vertices in REPS z planes.
+// consecutive x vertices in REPS (= 2) consecutive z planes.
 template <int TX_, int TY_, int TZ_>
 struct Shape {
     static constexpr int TX = TX_, TY = TY_, TZ = TZ_;
@@ -70,17 +70,16 @@ __device__ __forceinline__ PK pack(int val, int code) {
     return (PK)val * 16 + code;
 }
 
-// argmax / argmin codes over the 15 packed candidates c[0..14].
+// argmax / argmin codes over the 15 packed candidates c[0..14] (two-input
+// min / max: measured faster here than the three-input DPX forms).
 __device__ __forceinline__ void best_codes(const int32_t (&c)[15], int& hi, int& lo) {
-    // three-input integer max / unsigned min: 7 + 7 operations, not 14 + 14
-    int a0 = __vimax3_s32(c[0], c[1], c[2]), a1 = __vimax3_s32(c[3], c[4], c[5]);
-    int a2 = __vimax3_s32(c[6], c[7], c[8]), a3 = __vimax3_s32(c[9], c[10], c[11]);
-    int a4 = __vimax3_s32(c[12], c[13], c[14]);
-    const int mx = __vimax3_s32(__vimax3_s32(a0, a1, a2), a3, a4);
-    unsigned b0 = __vimin3_u32(c[0], c[1], c[2]), b1 = __vimin3_u32(c[3], c[4], c[5]);
-    unsigned b2 = __vimin3_u32(c[6], c[7], c[8]), b3 = __vimin3_u32(c[9], c[10], c[11]);
-    unsigned b4 = __vimin3_u32(c[12], c[13], c[14]);
-    const unsigned mn = __vimin3_u32(__vimin3_u32(b0, b1, b2), b3, b4);
+    int mx = c[0];
+    unsigned mn = (unsigned)c[0];
+#pragma unroll
+    for (int k = 1; k < 15; ++k) {
+        mx = max(mx, c[k]);
+        mn = min(mn, (unsigned)c[k]);
+    }
     hi = mx & 15;
     lo = (int)(mn & 15u);
 }
@@ -108,29 +107,47 @@ __device__ __forceinline__ void load_row(const int* r, int (&o)[6]) {
     o[5] = r[4];
 }
 
-template <typename PK, typename S = Tile>
+// COUNT: add the tile's minima / maxima to nmin / nmax.
+template <typename PK, typename S = Tile, bool COUNT = true>
 __device__ __forceinline__ void tile_compute(const int* buf, const GridInfo& g, int x0, int y0,
                                              int z0, const int32_t* s_off, int32_t* __restrict__ asc,
                                              int32_t* __restrict__ desc, uint32_t& nmin,
                                              uint32_t& nmax) {
+    static_assert(S::REPS == 2, "a thread takes two consecutive z planes");
     const int tid = threadIdx.x;
     const int xq = tid % S::XQ, ly = (tid / S::XQ) % S::TY, lzq = tid / S::LAYER;
     const int gx0 = x0 + 4 * xq, gy = y0 + ly;
     if (gx0 >= g.nx || gy >= g.ny) return;
+    // Rows around the thread's 4 vertices in plane z: A (z-1, y), B (z-1, y-1),
+    // C (z, y-1), D (z, y), E (z, y+1), F (z+1, y), G (z+1, y+1).  For plane
+    // z+1, A = D, B = C, D = F and E = G of plane z: only C, F, G are read.
+    const int lz0 = 2 * lzq;
+    const int* b = buf + (lz0 + 1) * S::PLANE + (ly + 1) * S::BX + 4 * xq + 4;
+    int A[6], B[6], C[6], D[6], E[6], F[6], G[6];
+    load_row(b - S::PLANE, A);
+    load_row(b - S::PLANE - S::BX, B);
+    load_row(b - S::BX, C);
+    load_row(b, D);
+    load_row(b + S::BX, E);
+    load_row(b + S::PLANE, F);
+    load_row(b + S::PLANE + S::BX, G);
 #pragma unroll
-    for (int rep = 0; rep < S::REPS; ++rep) {
-        const int lz = lzq + S::ZL * rep;
-        const int gz = z0 + lz;
+    for (int rep = 0; rep < 2; ++rep) {
+        const int gz = z0 + lz0 + rep;
         if (gz >= g.nz) break;
-        const int* b = buf + (lz + 1) * S::PLANE + (ly + 1) * S::BX + 4 * xq + 4;
-        int A[6], B[6], C[6], D[6], E[6], F[6], G[6];
-        load_row(b - S::PLANE, A);
-        load_row(b - S::PLANE - S::BX, B);
-        load_row(b - S::BX, C);
-        load_row(b, D);
-        load_row(b + S::BX, E);
-        load_row(b + S::PLANE, F);
-        load_row(b + S::PLANE + S::BX, G);
+        if (rep == 1) {
+#pragma unroll
+            for (int t = 0; t < 6; ++t) {
+                A[t] = D[t];
+                B[t] = C[t];
+                D[t] = F[t];
+                E[t] = G[t];
+            }
+            b += S::PLANE;
+            load_row(b - S::BX, C);
+            load_row(b + S::PLANE, F);
+            load_row(b + S::PLANE + S::BX, G);
+        }
         int hi_code[4], lo_code[4];
 #pragma unroll
         for (int i = 0; i < 4; ++i) {
@@ -149,8 +166,10 @@ __device__ __forceinline__ void tile_compute(const int* buf, const GridInfo& g, 
         for (int i = 0; i < 4; ++i) {
             out_hi[i] = v0 + i + s_off[hi_code[i]];
             out_lo[i] = v0 + i + s_off[lo_code[i]];
-            nmax += hi_code[i] == 14 && gx0 + i < g.nx;
-            nmin += lo_code[i] == 14 && gx0 + i < g.nx;
+            if (COUNT) {
+                nmax += hi_code[i] == 14 && gx0 + i < g.nx;
+                nmin += lo_code[i] == 14 && gx0 + i < g.nx;
+            }
         }
 #ifdef MSC_DEBUG_BOUNDS
         if (v0 < 0) return;
@@ -207,7 +226,7 @@ __device__ __forceinline__ void flush_counts(uint32_t nmin, uint32_t nmax, uint3
     }
 }
 
-template <typename PK>
+template <typename PK, bool COUNT>
 __global__ void __launch_bounds__(kThreads, 4) k_steepest_tma(const __grid_constant__ CUtensorMap map,
                                                           const GridInfo g, int32_t* asc,
                                                           int32_t* desc, uint32_t* extrema,
@@ -253,19 +272,19 @@ __global__ void __launch_bounds__(kThreads, 4) k_steepest_tma(const __grid_const
             mark_outside(buf[b], g, x0, y0, z0);
             __syncthreads();
         }
-        tile_compute<PK>(buf[b], g, x0, y0, z0, s_off, asc, desc, nmin, nmax);
+        tile_compute<PK, Tile, COUNT>(buf[b], g, x0, y0, z0, s_off, asc, desc, nmin, nmax);
         __syncthreads();
         if (tid == 0 && tile + 2 * (int64_t)gridDim.x < g.ntiles) {
             fence_proxy_async_smem();
             issue(tile + 2 * (int64_t)gridDim.x, b);
         }
     }
-    flush_counts(nmin, nmax, extrema);
+    if (COUNT) flush_counts(nmin, nmax, extrema);
 }
 
 // Same stencil with plain coalesced loads (grids whose rows TMA cannot
 // address: nx not a multiple of 4, or an unaligned base pointer).
-template <typename PK>
+template <typename PK, bool COUNT>
 __global__ void __launch_bounds__(kThreads) k_steepest_ld(const int32_t* __restrict__ order,
                                                          const GridInfo g, int32_t* asc,
                                                          int32_t* desc, uint32_t* extrema) {
@@ -287,10 +306,10 @@ __global__ void __launch_bounds__(kThreads) k_steepest_ld(const int32_t* __restr
             buf[i] = val;
         }
         __syncthreads();
-        tile_compute<PK>(buf, g, x0, y0, z0, s_off, asc, desc, nmin, nmax);
+        tile_compute<PK, Tile, COUNT>(buf, g, x0, y0, z0, s_off, asc, desc, nmin, nmax);
         __syncthreads();
     }
-    flush_counts(nmin, nmax, extrema);
+    if (COUNT) flush_counts(nmin, nmax, extrema);
 }
 
 // ----------------------------------------------------------------------------
@@ -457,7 +476,8 @@ int run_steepest_grid(const int32_t* order, msc_grid gd, int32_t* asc, int32_t* 
     const bool tma = allow_tma && make_tensor_map_3d(&map, order, 4, gd.nx, gd.ny, gd.nz, BX, BY, BZ);
     int occ = 1;
     if (tma) {
-        auto kern = packed ? k_steepest_tma<int32_t> : k_steepest_tma<int64_t>;
+        auto kern = extrema ? (packed ? k_steepest_tma<int32_t, true> : k_steepest_tma<int64_t, true>)
+                            : (packed ? k_steepest_tma<int32_t, false> : k_steepest_tma<int64_t, false>);
         MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)sms * std::max(occ, 1)));
         {
@@ -465,7 +485,8 @@ int run_steepest_grid(const int32_t* order, msc_grid gd, int32_t* asc, int32_t* 
             kern<<<(unsigned)grid, kThreads, 0, s>>>(map, g, asc, desc, extrema, status);
         }
     } else {
-        auto kern = packed ? k_steepest_ld<int32_t> : k_steepest_ld<int64_t>;
+        auto kern = extrema ? (packed ? k_steepest_ld<int32_t, true> : k_steepest_ld<int64_t, true>)
+                            : (packed ? k_steepest_ld<int32_t, false> : k_steepest_ld<int64_t, false>);
         MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
         const int64_t grid = std::max<int64_t>(1, std::min<int64_t>(g.ntiles, (int64_t)sms * std::max(occ, 1)));
         {
