@@ -5,8 +5,8 @@
 // Grid kernel: persistent CTAs walk 32x8x8 vertex tiles.  Each tile's
 // order values plus a halo (4 cells in x to keep the TMA x coordinate
 // 16-byte aligned, 1 cell in y and z) land in shared memory through one 3D
-// TMA box (40x10x10 int32), double-buffered against the compute of the
-// previous tile.  Cells outside the grid get -1, which loses every signed
+// TMA box (40x10x10 int32), three boxes in flight against the compute of the
+// previous tiles.  Cells outside the grid get -1, which loses every signed
 // max and (as 0xffffffff) every unsigned min, so border vertices see only
 // their in-grid neighbours.  A thread handles four consecutive x vertices
 // in two z planes, reading each neighbour row once as an int4 plus edge
@@ -26,6 +26,7 @@ namespace {
 
 constexpr int kThreads = 256;
 constexpr uint32_t kWaitLimit = 1u << 22;
+constexpr int kStages = 3;  // TMA boxes in flight per CTA (3 x 16 000 B of shared memory)
 
 // A tile of TX x TY x TZ vertices and its shared-memory box (4 halo cells
 // in x, keeping 16-byte alignment, 1 in y and z).  A thread takes four
@@ -231,13 +232,12 @@ __global__ void __launch_bounds__(kThreads, 4) k_steepest_tma(const __grid_const
                                                           const GridInfo g, int32_t* asc,
                                                           int32_t* desc, uint32_t* extrema,
                                                           int32_t* status) {
-    __shared__ alignas(128) int buf[2][BOX];
-    __shared__ alignas(8) uint64_t bar[2];
+    __shared__ alignas(128) int buf[kStages][BOX];
+    __shared__ alignas(8) uint64_t bar[kStages];
     __shared__ int32_t s_off[15];
     const int tid = threadIdx.x;
     if (tid == 0) {
-        mbar_init(&bar[0], 1);
-        mbar_init(&bar[1], 1);
+        for (int q = 0; q < kStages; ++q) mbar_init(&bar[q], 1);
         fence_mbar_init();
     }
     if (tid < 15)
@@ -250,33 +250,34 @@ __global__ void __launch_bounds__(kThreads, 4) k_steepest_tma(const __grid_const
         tma_load_3d(buf[b], &map, x0 - 4, y0 - 1, z0 - 1, &bar[b]);
     };
     int64_t tile = blockIdx.x;
-    if (tid == 0) {
-        if (tile < g.ntiles) issue(tile, 0);
-        if (tile + gridDim.x < g.ntiles) issue(tile + gridDim.x, 1);
-    }
-    uint32_t phase[2] = {0u, 0u};
+    if (tid == 0)
+        for (int q = 0; q < kStages; ++q)
+            if (tile + q * (int64_t)gridDim.x < g.ntiles) issue(tile + q * (int64_t)gridDim.x, q);
+    uint32_t phase[kStages] = {};
     uint32_t nmin = 0, nmax = 0;
     for (int it = 0; tile < g.ntiles; ++it, tile += gridDim.x) {
-        const int b = it & 1;
+        const int b = it % kStages;
         const bool ok = mbar_wait(&bar[b], phase[b], kWaitLimit);
-        if (__syncthreads_or(!ok)) {  // never expected: give up cleanly
+        if (ok) {
+            int x0, y0, z0;
+            tile_coords(g, tile, x0, y0, z0);
+            if (box_crosses_border(g, x0, y0, z0)) {  // block-uniform
+                mark_outside(buf[b], g, x0, y0, z0);
+                __syncthreads();
+            }
+            tile_compute<PK, Tile, COUNT>(buf[b], g, x0, y0, z0, s_off, asc, desc, nmin, nmax);
+        }
+        // one barrier per tile: the buffer is free again, and a failed wait
+        // (never expected) is seen by every thread
+        if (__syncthreads_or(!ok)) {
             if (tid == 0) record_error(status, MSC_ERR_INTERNAL);
-            mbar_wait(&bar[b], phase[b], kWaitLimit);
-            mbar_wait(&bar[b ^ 1], phase[b ^ 1], kWaitLimit);
+            for (int q = 0; q < kStages; ++q) mbar_wait(&bar[q], phase[q], kWaitLimit);
             return;
         }
         phase[b] ^= 1u;
-        int x0, y0, z0;
-        tile_coords(g, tile, x0, y0, z0);
-        if (box_crosses_border(g, x0, y0, z0)) {
-            mark_outside(buf[b], g, x0, y0, z0);
-            __syncthreads();
-        }
-        tile_compute<PK, Tile, COUNT>(buf[b], g, x0, y0, z0, s_off, asc, desc, nmin, nmax);
-        __syncthreads();
-        if (tid == 0 && tile + 2 * (int64_t)gridDim.x < g.ntiles) {
+        if (tid == 0 && tile + kStages * (int64_t)gridDim.x < g.ntiles) {
             fence_proxy_async_smem();
-            issue(tile + 2 * (int64_t)gridDim.x, b);
+            issue(tile + kStages * (int64_t)gridDim.x, b);
         }
     }
     if (COUNT) flush_counts(nmin, nmax, extrema);
