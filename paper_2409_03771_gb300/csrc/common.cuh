@@ -19,7 +19,7 @@ __device__ __forceinline__ void record_error(int32_t* status, int32_t code) {
 // Debug builds (-DMSC_DEBUG_BOUNDS) check data-dependent addresses before
 // the access: a violation records `code` in the status word and skips the
 // access.  Release builds compile the check away.
-#ifdef MSC_DEBUG_BOUNDS
+#if defined(MSC_DEBUG_BOUNDS) || defined(MSC_GUARDS)
 #define MSC_GUARD(cond, status, code) if (!(cond)) record_error((status), (code)); else
 #else
 #define MSC_GUARD(cond, status, code)
