@@ -229,13 +229,26 @@ __global__ void __launch_bounds__(kThreads) k_cc_local(const uint8_t* __restrict
 // (without the other two): 512 + 448 + 49 = 1009 per full tile.
 constexpr int kShell = CX * CY + CX * (CZ - 1) + (CY - 1) * (CZ - 1);
 
+// The crossing edges of one tile mostly join the same few pairs of
+// tile-local components.  Each tile's distinct pairs (a, b) are collected in
+// a shared-memory hash set (after a warp-level skip of repeated pairs in
+// consecutive lanes), then united in parallel, one thread per pair; a pair
+// that finds the set full is united at once.
+constexpr int kPairSlots = 256;
+
 __global__ void __launch_bounds__(kThreads) k_cc_merge(const CcGrid g, int32_t* label, int32_t* status) {
+    __shared__ unsigned long long s_pair[kPairSlots];
     const int npos = g.conn == 6 ? 3 : 7;
+    const int lane = threadIdx.x & 31;
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         int x0, y0, z0;
         cc_tile_coords(g, t, x0, y0, z0);
-        for (int s = threadIdx.x; s < kShell; s += kThreads) {
-            int lx, ly, lz;
+        for (int i = threadIdx.x; i < kPairSlots; i += kThreads) s_pair[i] = ~0ull;
+        __syncthreads();
+        // the trip count is warp-uniform: kShell rounded up to whole warps
+        for (int s0 = threadIdx.x - lane; s0 < kShell; s0 += kThreads) {
+            const int s = s0 + lane;
+            int lx = 0, ly = 0, lz = 0;
             if (s < CX * CY) {
                 lx = s % CX;
                 ly = s / CX;
@@ -252,20 +265,36 @@ __global__ void __launch_bounds__(kThreads) k_cc_merge(const CcGrid g, int32_t* 
                 lx = CX - 1;
             }
             const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-            if (gx >= g.nx || gy >= g.ny || gz >= g.nz) continue;
+            const bool in = s < kShell && gx < g.nx && gy < g.ny && gz < g.nz;
             const int64_t v = gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz);
-            int32_t a = -2;  // loaded lazily
+            const int32_t a = in ? label[v] : -1;
             for (int o = 0; o < npos; ++o) {
                 const int dx = c_pos[o][0], dy = c_pos[o][1], dz = c_pos[o][2];
-                if (lx + dx < CX && ly + dy < CY && lz + dz < CZ) continue;  // inside the tile
                 const int ux = gx + dx, uy = gy + dy, uz = gz + dz;
-                if (ux >= g.nx || uy >= g.ny || uz >= g.nz) continue;
-                if (a == -2) a = label[v];
-                if (a < 0) break;
-                const int32_t b = label[ux + (int64_t)g.nx * (uy + (int64_t)g.ny * uz)];
-                if (b >= 0 && b != a) union_g(label, a, b, status);
+                const bool cross = in && a >= 0 && !(lx + dx < CX && ly + dy < CY && lz + dz < CZ) && ux < g.nx &&
+                                   uy < g.ny && uz < g.nz;
+                const int32_t b = cross ? label[ux + (int64_t)g.nx * (uy + (int64_t)g.ny * uz)] : -1;
+                const bool want = cross && b >= 0 && b != a;
+                const int32_t pa = __shfl_up_sync(0xffffffffu, want ? a : -1, 1);
+                const int32_t pb = __shfl_up_sync(0xffffffffu, want ? b : -1, 1);
+                if (want && (lane == 0 || pa != a || pb != b)) {
+                    const unsigned long long key = ((unsigned long long)(uint32_t)a << 32) | (uint32_t)b;
+                    uint32_t h = (uint32_t)((key * 0x9e3779b97f4a7c15ull) >> 56) & (kPairSlots - 1);
+                    bool placed = false;
+                    for (int probe = 0; probe < 16 && !placed; ++probe, h = (h + 1) & (kPairSlots - 1)) {
+                        const unsigned long long old = atomicCAS(&s_pair[h], ~0ull, key);
+                        placed = old == ~0ull || old == key;
+                    }
+                    if (!placed) union_g(label, a, b, status);  // set full: unite now
+                }
             }
         }
+        __syncthreads();
+        for (int i = threadIdx.x; i < kPairSlots; i += kThreads) {
+            const unsigned long long key = s_pair[i];
+            if (key != ~0ull) union_g(label, (int32_t)(key >> 32), (int32_t)(uint32_t)key, status);
+        }
+        __syncthreads();
     }
 }
 
@@ -292,11 +321,13 @@ __global__ void __launch_bounds__(kFlatThreads) k_flatten(int32_t* label, int64_
             r[j] = l[j];
             open |= (l[j] >= 0 ? 1u : 0u) << j;
         }
+        // cached loads: a label read stale is still an ancestor of the
+        // vertex (labels only decrease), so following it stays correct
 #pragma unroll
         for (int h = 0; h < kFlatHops; ++h) {
             int32_t w[kFlatPer];
 #pragma unroll
-            for (int j = 0; j < kFlatPer; ++j) w[j] = (open >> j & 1u) ? ld_volatile_s32(label + r[j]) : 0;
+            for (int j = 0; j < kFlatPer; ++j) w[j] = (open >> j & 1u) ? label[r[j]] : 0;
 #pragma unroll
             for (int j = 0; j < kFlatPer; ++j)
                 if (open >> j & 1u) {
@@ -358,7 +389,6 @@ __global__ void k_mesh_link_k(const int32_t* __restrict__ row, const int32_t* __
 // the smaller label).
 __global__ void __launch_bounds__(kSamples) k_mesh_sample(const int32_t* label, int32_t n, int32_t* frequent) {
     __shared__ int32_t s[kSamples];
-    __shared__ int32_t s_best[2];  // label, run length
     const int t = threadIdx.x;
     const uint64_t mixed = (uint64_t)(t + 1) * 0x9e3779b97f4a7c15ull;
     s[t] = label[(int64_t)((mixed >> 11) % (uint64_t)n)];
