@@ -177,6 +177,7 @@ def algorithmic_bytes(label, n, nm, nnz):
         "order.pass_first": 12 * n,      # read f, write (key, id)
         "order.pass": 16 * n,            # read and write (key, id)
         "order.pass_last": 16 * n,       # read (key, id), write (id, position) pairs
+        "order.split": 16 * n,           # read the pairs, write them by sub-bucket of 2^15 ids
         "order.scatter": 12 * n,         # read the pairs, write order
         "steepest.grid": 12 * n,         # read order, write asc + desc
         "msid.insert": 12 * n,           # read asc + desc, write slot

@@ -13,19 +13,16 @@
 // per-warp counters), publishes its per-digit counts to a decoupled
 // look-back array, sums its predecessors' counts and scatters through
 // shared memory.  The last pass files (vertex id, position) pairs into
-// buckets of consecutive ids, and a thread-block cluster scatters each
-// bucket into its distributed shared memory and writes order[id] =
-// position out as whole lines (k_pair_scatter_dsmem).
+// buckets of consecutive ids; the order field is their inverse
+// permutation, written through shared memory: the buckets are split into
+// sub-buckets of 2^15 ids, each scattered into one CTA's shared memory and
+// written out as whole lines (k_pair_split, k_pair_scatter_local).
 #include <cuda_runtime.h>
-
-#include <cooperative_groups.h>
 
 #include <algorithm>
 #include <utility>
 
 #include "sort.cuh"
-
-namespace cg = cooperative_groups;
 
 namespace msc {
 #ifdef MSC_DEBUG_BOUNDS
@@ -43,8 +40,7 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 // The last pass of the vertex order files (id, position) pairs into
 // buckets of 2^shift consecutive ids; bucket b holds exactly the ids
 // [b << shift, (b + 1) << shift) and so occupies pair slots of the same
-// range.  At most kMaxBuckets buckets; the shift is chosen so that one
-// bucket matches the id range a cluster's shared memory covers.
+// range.  At most kMaxBuckets buckets (see bucket_shift).
 constexpr int kMaxBuckets = 256;
 constexpr int kFillStride = 32;  // one 128-byte line per bucket counter: the
                                  // tiles' reservations spread over L2 slices
@@ -515,196 +511,148 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
     }
 }
 
-// order[ids[slot]] = pos[slot] for every filed pair (fallback when no
-// cluster can be launched): scattered 4-byte writes straight to memory.
-__global__ void __launch_bounds__(256) k_pair_scatter(const int32_t* __restrict__ ids,
-                                                      const uint32_t* __restrict__ pos, int64_t n,
-                                                      int32_t* __restrict__ order, int32_t* status) {
-    constexpr int kPer = kSortTile / 256;
-    for (int64_t t = blockIdx.x; t * kSortTile < n; t += gridDim.x) {
-        int32_t id[kPer];
-        uint32_t ps[kPer];
-#pragma unroll
-        for (int j = 0; j < kPer; ++j) {
-            const int64_t i = t * kSortTile + j * 256 + threadIdx.x;
-            id[j] = i < n ? __ldcs(ids + i) : -1;
-            ps[j] = i < n ? __ldcs(pos + i) : 0u;
-        }
-#pragma unroll
-        for (int j = 0; j < kPer; ++j)
-            if (id[j] >= 0) {
-                MSC_GUARD((int64_t)id[j] < n, status, -104)
-                order[id[j]] = (int32_t)ps[j];
-            }
-    }
+// Width of the id buckets the last pass files pairs into: 2^19 ids at
+// least (so that each bucket splits into 16 sub-buckets of 2^15), and at
+// most kMaxBuckets buckets.
+int bucket_shift(int64_t n) {
+    return std::max(19, ceil_log2(ceil_div(std::max<int64_t>(n, 1), kMaxBuckets)));
 }
 
-// The same through distributed shared memory.  A cluster of C CTAs holds
-// C * 2^15 consecutive entries of the order array in shared memory (128 KiB
-// per CTA).  For each bucket (or part of a bucket that the cluster
-// covers) its CTAs stream the bucket's pairs, store every position into
-// the shared-memory slice of the CTA that owns the id (a remote store
-// within the cluster), synchronise the cluster, and write their slices out
-// as whole lines.  DRAM sees each pair read once and each order entry
-// written once.
-constexpr int kSliceLog2 = 15;
-constexpr int kSliceIds = 1 << kSliceLog2;
-constexpr int kScatterThreads = 1024;
+// Two-level order inversion.  (1) k_pair_split: every
+// chunk of 4096 filed pairs (a chunk lies inside one bucket of 2^shift ids)
+// re-files its pairs into sub-buckets of 2^15 ids; sub-bucket j holds
+// exactly the ids j * 2^15 + [0, 2^15) and so fills those pair slots.  A
+// chunk reserves its share of each sub-bucket with one atomic per
+// sub-bucket and regroups its pairs in shared memory, so that each run is
+// written with consecutive lanes.  (2) k_pair_scatter_local: one CTA per
+// sub-bucket stores its 2^15 positions into a 128 KiB shared-memory slice
+// of the order array and writes the slice out as whole lines.
+constexpr int kSubLog2 = 15;
+constexpr int kSubIds = 1 << kSubLog2;
+constexpr int kSplitThreads = 512;
+constexpr int kSplitChunk = 4096;
+constexpr int kSplitPer = kSplitChunk / kSplitThreads;  // 8
+constexpr int kMaxSub = 1 << 8;  // sub-buckets per bucket (shift <= 23)
 
-template <int C>
-__global__ void __launch_bounds__(kScatterThreads, 1) k_pair_scatter_dsmem(const int32_t* __restrict__ ids,
-                                                                          const uint32_t* __restrict__ pos,
-                                                                          int64_t n, int bucket_shift,
-                                                                          int32_t* __restrict__ order,
-                                                                          int32_t* status) {
-    extern __shared__ __align__(16) int32_t slice[];  // kSliceIds
-    cg::cluster_group cl = cg::this_cluster();
-    const int rank = (int)cl.block_rank();
-    const int64_t ncl = gridDim.x / C, cid = blockIdx.x / C;
-    const int64_t W = int64_t(1) << bucket_shift;
-    constexpr int64_t kCover = (int64_t)C * kSliceIds;
-    const int64_t subs = W > kCover ? W / kCover : 1;  // W and kCover are powers of two
-    const int64_t nb = (n + W - 1) >> bucket_shift;
-    for (int64_t job = cid; job < nb * subs; job += ncl) {
-        const int64_t b = job / subs, sr = job - b * subs;
-        const int64_t s0 = b * W, s1 = min(n, s0 + W);  // the bucket's slots = its ids
-        const int64_t lo = s0 + sr * kCover;            // first id of this part
-        // 16-byte loads of 4 consecutive pairs, kUnroll groups per thread in
-        // flight (loads first, then the remote stores); a ragged end of the
-        // bucket goes pair by pair
-        constexpr int kUnroll = 2;
-        constexpr int64_t kStep = (int64_t)C * kScatterThreads;  // groups of 4 per sweep
-        const int64_t groups = (s1 - s0) >> 2;
-        auto put = [&](int32_t id, uint32_t p) {
-            const int64_t off = (int64_t)id - lo;
-            if (off >= 0 && off < kCover)
-                *cl.map_shared_rank(slice + (off & (kSliceIds - 1)), (unsigned)(off >> kSliceLog2)) = (int32_t)p;
-            else if (subs == 1)
-                record_error(status, MSC_ERR_INTERNAL);  // an id outside its bucket
-        };
-        for (int64_t g0 = (int64_t)rank * kScatterThreads + threadIdx.x; g0 < groups; g0 += kUnroll * kStep) {
-            int4 id[kUnroll];
-            uint4 p[kUnroll];
+__global__ void __launch_bounds__(kSplitThreads) k_pair_split(const int32_t* __restrict__ ids_in,
+                                                              const uint32_t* __restrict__ pos_in, int64_t n,
+                                                              int shift, uint32_t* sub_fill,
+                                                              int32_t* __restrict__ ids_out,
+                                                              uint32_t* __restrict__ pos_out, int32_t* status) {
+    __shared__ int32_t s_id[kSplitChunk];
+    __shared__ uint32_t s_pos[kSplitChunk];
+    __shared__ uint32_t s_cnt[kMaxSub];   // counts, then chunk-local starts
+    __shared__ uint32_t s_base[kMaxSub];  // first slot of the chunk's run in each sub-bucket
+    __shared__ uint32_t s_w[kSplitThreads / 32];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int nsub = 1 << (shift - kSubLog2);
+    for (int64_t c0 = (int64_t)blockIdx.x * kSplitChunk; c0 < n; c0 += (int64_t)gridDim.x * kSplitChunk) {
+        const int cnt = (int)min((int64_t)kSplitChunk, n - c0);
+        const int64_t s0 = (c0 >> shift) << shift;  // first id of the chunk's bucket
+        for (int i = tid; i < nsub; i += kSplitThreads) s_cnt[i] = 0;
+        __syncthreads();
+        int32_t id[kSplitPer];
+        uint32_t ps[kSplitPer], rank[kSplitPer];
 #pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                const int64_t g = g0 + u * kStep;
-                if (g < groups) {
-                    id[u] = __ldcs(reinterpret_cast<const int4*>(ids + s0) + g);
-                    p[u] = __ldcs(reinterpret_cast<const uint4*>(pos + s0) + g);
-                } else {
-                    id[u] = make_int4(-1, -1, -1, -1);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < kUnroll; ++u) {
-                if (id[u].x < 0) continue;
-                put(id[u].x, p[u].x);
-                put(id[u].y, p[u].y);
-                put(id[u].z, p[u].z);
-                put(id[u].w, p[u].w);
+        for (int k = 0; k < kSplitPer; ++k) {
+            const int i = tid + k * kSplitThreads;
+            id[k] = -1;
+            if (i < cnt) {
+                id[k] = __ldcs(ids_in + c0 + i);
+                ps[k] = __ldcs(pos_in + c0 + i);
+                const int64_t off = (int64_t)id[k] - s0;
+                MSC_GUARD(off >= 0 && off < (int64_t(1) << shift), status, -106)
+                rank[k] = atomicAdd(&s_cnt[off >> kSubLog2], 1u);
             }
         }
-        for (int64_t sl = s0 + groups * 4 + (int64_t)rank * kScatterThreads + threadIdx.x; sl < s1; sl += kStep)
-            put(__ldcs(ids + sl), __ldcs(pos + sl));
-        cl.sync();  // every remote store has landed
-        const int64_t m0 = lo + (int64_t)rank * kSliceIds;  // a multiple of 2^15
-        const int64_t m1 = min(m0 + kSliceIds, s1);
-        const int64_t full = m1 > m0 ? (m1 - m0) >> 2 : 0;
-        for (int64_t i = threadIdx.x; i < full; i += kScatterThreads)
-            reinterpret_cast<int4*>(order + m0)[i] = reinterpret_cast<const int4*>(slice)[i];
-        for (int64_t i = full * 4 + threadIdx.x; m0 + i < m1; i += kScatterThreads) order[m0 + i] = slice[i];
-        cl.sync();  // slices are free for the next part
-    }
-}
-
-struct ScatterPlan {
-    int cluster = 0;  // 16 or 8 CTAs; 0: no cluster fits, plain scatter
-    int clusters = 0; // clusters resident at once
-    int shift = 0;    // log2 ids per bucket
-};
-
-template <int C>
-int dsmem_clusters() {
-    auto kern = k_pair_scatter_dsmem<C>;
-    const int smem = kSliceIds * 4;
-    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem) != cudaSuccess) return 0;
-    if (C > 8 && cudaFuncSetAttribute(kern, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) != cudaSuccess)
-        return 0;
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3(C);
-    cfg.blockDim = dim3(kScatterThreads);
-    cfg.dynamicSmemBytes = smem;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = C;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    int num = 0;
-    if (cudaOccupancyMaxActiveClusters(&num, kern, &cfg) != cudaSuccess) {
-        cudaGetLastError();
-        return 0;
-    }
-    return num;
-}
-
-// Cluster shape and bucket width for n ids (cached per device).
-ScatterPlan scatter_plan(int64_t n) {
-    static ScatterPlan per_dev[64];
-    static bool done[64] = {};
-    const int dev = current_device().id & 63;
-    if (!done[dev]) {
-        ScatterPlan p;
-        if ((p.clusters = dsmem_clusters<16>()) > 0) p.cluster = 16;
-        else if ((p.clusters = dsmem_clusters<8>()) > 0) p.cluster = 8;
-        per_dev[dev] = p;
-        done[dev] = true;
-    }
-    ScatterPlan p = per_dev[dev];
-    const int cover_log2 = p.cluster == 16 ? kSliceLog2 + 4 : kSliceLog2 + 3;
-    p.shift = std::max(cover_log2, ceil_log2(ceil_div(std::max<int64_t>(n, 1), kMaxBuckets)));
-    return p;
-}
-
-int launch_pair_scatter(const ScatterPlan& p, const int32_t* ids, const uint32_t* pos, int64_t n, int32_t* order,
-                        int32_t* status, cudaStream_t s) {
-    if (p.cluster == 0) {
-        const int64_t tiles = ceil_div(n, kSortTile);
-        const int grid = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (int64_t)current_device().sms * 8));
-        {
-            TraceScope ts_("order.scatter", s);
-            k_pair_scatter<<<grid, 256, 0, s>>>(ids, pos, n, order, status);
+        __syncthreads();
+        // chunk-local exclusive starts over the nsub (<= 256) sub-buckets, and
+        // the chunk's reservation in each of them
+        const uint32_t c = tid < nsub ? s_cnt[tid] : 0u;
+        uint32_t incl = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
         }
-        MSC_LAUNCHED();
-        return MSC_OK;
+        if (lane == 31) s_w[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0;
+        for (int w = 0; w < warp; ++w) before += s_w[w];
+        if (tid < nsub) {
+            s_base[tid] = c ? atomicAdd(&sub_fill[(s0 >> kSubLog2) + tid], c) : 0u;
+            s_cnt[tid] = before + incl - c;
+        }
+        __syncthreads();
+#pragma unroll
+        for (int k = 0; k < kSplitPer; ++k)
+            if (id[k] >= 0) {
+                const uint32_t j = s_cnt[(uint32_t)(id[k] - s0) >> kSubLog2] + rank[k];
+                s_id[j] = id[k];
+                s_pos[j] = ps[k];
+            }
+        __syncthreads();
+        for (int i = tid; i < cnt; i += kSplitThreads) {
+            const int32_t v = s_id[i];
+            const int sub = (int)((uint32_t)(v - s0) >> kSubLog2);
+            const uint32_t slot = s_base[sub] + (uint32_t)i - s_cnt[sub];
+            const int64_t dst = s0 + ((int64_t)sub << kSubLog2) + slot;
+            MSC_GUARD(slot < (uint32_t)kSubIds && dst < n, status, -107) {
+                ids_out[dst] = v;
+                pos_out[dst] = s_pos[i];
+            }
+        }
+        __syncthreads();
     }
-    const int64_t W = int64_t(1) << p.shift;
-    const int64_t cover = (int64_t)p.cluster << kSliceLog2;
-    const int64_t jobs = ceil_div(n, W) * std::max<int64_t>(1, W / cover);
-    const int64_t ncl = std::max<int64_t>(1, std::min<int64_t>(jobs, p.clusters));
-    cudaLaunchConfig_t cfg{};
-    cfg.gridDim = dim3((unsigned)(ncl * p.cluster));
-    cfg.blockDim = dim3(kScatterThreads);
-    cfg.dynamicSmemBytes = kSliceIds * 4;
-    cfg.stream = s;
-    cudaLaunchAttribute at[1];
-    at[0].id = cudaLaunchAttributeClusterDimension;
-    at[0].val.clusterDim.x = p.cluster;
-    at[0].val.clusterDim.y = 1;
-    at[0].val.clusterDim.z = 1;
-    cfg.attrs = at;
-    cfg.numAttrs = 1;
-    cudaError_t e;
+}
+
+__global__ void __launch_bounds__(1024) k_pair_scatter_local(const int32_t* __restrict__ ids,
+                                                             const uint32_t* __restrict__ pos, int64_t n,
+                                                             int32_t* __restrict__ order, int32_t* status) {
+    extern __shared__ __align__(16) int32_t slice[];  // kSubIds
+    const int64_t nsub = (n + kSubIds - 1) >> kSubLog2;
+    for (int64_t sb = blockIdx.x; sb < nsub; sb += gridDim.x) {
+        const int64_t s0 = sb << kSubLog2, s1 = min(n, s0 + kSubIds);
+        const int cnt = (int)(s1 - s0);
+        for (int i = threadIdx.x; i < cnt; i += 1024) {
+            const int32_t id = __ldcs(ids + s0 + i);
+            const uint32_t p = __ldcs(pos + s0 + i);
+            const int64_t off = (int64_t)id - s0;
+            MSC_GUARD(off >= 0 && off < cnt, status, -108)
+            slice[off] = (int32_t)p;
+        }
+        __syncthreads();
+        const int full = cnt >> 2;
+        for (int i = threadIdx.x; i < full; i += 1024)
+            reinterpret_cast<int4*>(order + s0)[i] = reinterpret_cast<const int4*>(slice)[i];
+        for (int i = full * 4 + threadIdx.x; i < cnt; i += 1024) order[s0 + i] = slice[i];
+        __syncthreads();
+    }
+}
+
+int launch_pair_split_scatter(int shift, const int32_t* ids, const uint32_t* pos, int32_t* ids2, uint32_t* pos2,
+                              uint32_t* sub_fill, int64_t n, int32_t* order, int32_t* status, cudaStream_t s) {
+    const int sms = current_device().sms;
+    MSC_TRY(cudaMemsetAsync(sub_fill, 0, (size_t)(ceil_div(n, kSubIds) + 1) * sizeof(uint32_t), s));
+    {
+        const int64_t chunks = ceil_div(n, kSplitChunk);
+        TraceScope ts_("order.split", s);
+        k_pair_split<<<(unsigned)std::min<int64_t>(chunks, (int64_t)sms * 4), kSplitThreads, 0, s>>>(
+            ids, pos, n, shift, sub_fill, ids2, pos2, status);
+    }
+    MSC_LAUNCHED();
+    static int configured_dev = -1;
+    if (configured_dev != current_device().id) {
+        MSC_TRY(cudaFuncSetAttribute(k_pair_scatter_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kSubIds * 4));
+        configured_dev = current_device().id;
+    }
+    const int64_t nsub = ceil_div(n, kSubIds);
     {
         TraceScope ts_("order.scatter", s);
-        e = p.cluster == 16 ? cudaLaunchKernelEx(&cfg, k_pair_scatter_dsmem<16>, ids, pos, n, p.shift, order, status)
-                            : cudaLaunchKernelEx(&cfg, k_pair_scatter_dsmem<8>, ids, pos, n, p.shift, order, status);
+        k_pair_scatter_local<<<(unsigned)std::min<int64_t>(nsub, (int64_t)sms), 1024, kSubIds * 4, s>>>(
+            ids2, pos2, n, order, status);
     }
-    if (e != cudaSuccess) {
-        cudaGetLastError();
-        return MSC_ERR_CUDA;
-    }
+    MSC_LAUNCHED();
     return MSC_OK;
 }
 
@@ -733,6 +681,7 @@ int launch_pass(const PassArgs<KeyT>& a, int64_t max_n, cudaStream_t s, const ch
 
 void size_sort_scratch(Sizer& s, int64_t n) {
     s.take<uint32_t>(8 * kBins + kCounterWords);
+    s.take<uint32_t>(ceil_div(std::max<int64_t>(n, 1), kSubIds) + 1);
     s.take<unsigned long long>((size_t)std::max<int64_t>(1, ceil_div(n, kSortTile)) * kBins);
 }
 
@@ -740,6 +689,7 @@ SortScratch carve_sort_scratch(Carver& c, int64_t n) {
     SortScratch sc;
     sc.hist = c.take<uint32_t>(8 * kBins + kCounterWords);
     sc.tile_counters = sc.hist + 8 * kBins;
+    sc.sub_fill = c.take<uint32_t>(ceil_div(std::max<int64_t>(n, 1), kSubIds) + 1);
     sc.max_tiles = std::max<int64_t>(1, ceil_div(n, kSortTile));
     sc.lookback = c.take<unsigned long long>((size_t)sc.max_tiles * kBins);
     return sc;
@@ -824,18 +774,19 @@ int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_
     a.vals_out = iout;
     a.pair_pos = kout;
     a.bucket_fill = sc.tile_counters + 8;
-    const ScatterPlan plan = scatter_plan(n);
-    a.bucket_shift = plan.shift;
+    a.bucket_shift = bucket_shift(n);
     a.hist = sc.hist + 3 * kBins;
     a.shift = 24;
     a.tile_counter = sc.tile_counters + 3;
     a.epoch = 4;
     if ((r = launch_pass<uint32_t, false, true>(a, n, s, "order.pass_last"))) return r;
-    return launch_pair_scatter(plan, iout, kout, n, order, status, s);
+    // the pass's inputs are free now: the split writes there
+    return launch_pair_split_scatter(a.bucket_shift, iout, kout, iin, kin, sc.sub_fill, n, order, status, s);
 }
 
 void size_seg_sort_scratch(Sizer& s, int count, int64_t tiles) {
     s.take<uint32_t>((size_t)count * kSegPasses * kBins + kCounterWords);
+    s.take<uint32_t>(ceil_div(std::max<int64_t>(tiles, 1) * kSortTile, kSubIds) + 1);
     s.take<unsigned long long>((size_t)std::max<int64_t>(1, tiles) * kBins);
 }
 
@@ -844,6 +795,7 @@ SortScratch carve_seg_sort_scratch(Carver& c, int count, int64_t tiles) {
     const size_t hist_words = (size_t)count * kSegPasses * kBins;
     sc.hist = c.take<uint32_t>(hist_words + kCounterWords);
     sc.tile_counters = sc.hist + hist_words;
+    sc.sub_fill = c.take<uint32_t>(ceil_div(std::max<int64_t>(tiles, 1) * kSortTile, kSubIds) + 1);
     sc.max_tiles = std::max<int64_t>(1, tiles);
     sc.lookback = c.take<unsigned long long>((size_t)sc.max_tiles * kBins);
     return sc;
@@ -910,14 +862,13 @@ int run_order_seg(const float* f, const SegTable& t, int32_t* order, uint32_t* k
     a.vals_out = iout;
     a.pair_pos = kout;
     a.bucket_fill = sc.tile_counters + 8;
-    const ScatterPlan plan = scatter_plan(t.total);
-    a.bucket_shift = plan.shift;
+    a.bucket_shift = bucket_shift(t.total);
     a.hist = sc.hist + 3 * kBins;
     a.shift = 24;
     a.tile_counter = sc.tile_counters + 3;
     a.epoch = 4;
     if ((r = launch_pass<uint32_t, false, true, true>(a, t.total, s, "order.pass_last"))) return r;
-    return launch_pair_scatter(plan, iout, kout, t.total, order, status, s);
+    return launch_pair_split_scatter(a.bucket_shift, iout, kout, iin, kin, sc.sub_fill, t.total, order, status, s);
 }
 
 int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* keys_alt,

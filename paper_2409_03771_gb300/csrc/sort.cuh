@@ -11,6 +11,7 @@ struct SortScratch {
     uint32_t* tile_counters;          // [8] dynamic tile ids, one per pass
     unsigned long long* lookback;     // [max_tiles][256] decoupled look-back words
     int64_t max_tiles;
+    uint32_t* sub_fill;               // order inversion: slots taken per sub-bucket of 2^15 ids
 };
 
 constexpr int kSortTile = 4096;       // keys per onesweep tile
