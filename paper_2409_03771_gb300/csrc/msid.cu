@@ -72,6 +72,10 @@ __global__ void k_ms_setcap(uint32_t* ctl, int64_t n, int64_t cap_max) {
     if ((long long)cap > cap_max) cap = (unsigned long long)cap_max;
     ctl[2] = (uint32_t)cap;  // cap_max <= 2^31
     ctl[3] = 0;
+    // home-slot multiplier: asc * cap / n as (asc * F) >> 32, F = cap * 2^32 / n
+    const unsigned long long f = (cap << 32) / (unsigned long long)n;
+    ctl[9] = (uint32_t)f;
+    ctl[10] = (uint32_t)(f >> 32);
 }
 
 __global__ void k_ms_clear(unsigned long long* keys, const uint32_t* ctl) {
@@ -88,9 +92,10 @@ __global__ void k_ms_clear(unsigned long long* keys, const uint32_t* ctl) {
 // pairs are nearly increasing, which keeps the rank writes and the final
 // lookups almost sequential too.
 __device__ __forceinline__ uint32_t home_slot(uint32_t asc, unsigned long long key, uint32_t cap,
-                                              int32_t n) {
+                                              unsigned long long f) {
     if (cap <= kCacheResidentSlots) return (uint32_t)mix64(key) & (cap - 1);  // fits in cache: spread
-    const uint32_t base = (uint32_t)(((unsigned long long)asc * cap) / (unsigned long long)n);
+    // asc * cap / n by a fixed-point multiply (f = cap * 2^32 / n), no division
+    const uint32_t base = (uint32_t)((unsigned long long)asc * (f >> 32) + (((unsigned long long)asc * (uint32_t)f) >> 32));
     return (base + (uint32_t)(mix64(key) & (kSpread - 1))) & (cap - 1);
 }
 
@@ -115,6 +120,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_insert(const int32_t* __restric
                                                         unsigned long long* keys, const uint32_t* ctl,
                                                         int32_t* ms, int32_t* status) {
     const uint32_t cap = ctl[2];
+    const unsigned long long f = (unsigned long long)ctl[9] | ((unsigned long long)ctl[10] << 32);
     const int lane = threadIdx.x & 31;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v - lane < n; v += stride) {
@@ -128,7 +134,7 @@ __global__ void __launch_bounds__(kThreads) k_ms_insert(const int32_t* __restric
         const uint32_t heads = __ballot_sync(0xffffffffu, head);
         const int my_head = 31 - __clz(heads & (0xffffffffu >> (31 - lane)));
         uint32_t slot = 0;
-        if (valid && head) slot = probe_insert(keys, cap, key, home_slot((uint32_t)asc[v], key, cap, n), status);
+        if (valid && head) slot = probe_insert(keys, cap, key, home_slot((uint32_t)asc[v], key, cap, f), status);
         slot = __shfl_sync(0xffffffffu, slot, my_head);
         if (valid) ms[v] = (int32_t)slot;
     }
