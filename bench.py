@@ -61,6 +61,21 @@ def dist_info():
     return rank, world, local
 
 
+def replica_throughput(ms_local, units_per_rank, world, device):
+    """Whole-job throughput of `world` independent replicas (one per GPU,
+    no data-path collective): the step time is the maximum over the ranks
+    (one all-reduce of the timing only), and every rank processes
+    units_per_rank units per step.  Returns (max ms per step, units/s)."""
+    import torch
+    import torch.distributed as dist
+
+    t = torch.tensor([float(ms_local)], device=device, dtype=torch.float64)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    ms_max = float(t.item())
+    return ms_max, world * units_per_rank / (ms_max / 1e3)
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -281,11 +296,7 @@ def run_ours(args):
     trace = msc.msc_trace_collect()
     check_status("timed region")
     ms = ev0.elapsed_time(ev1) / args.steps
-    t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if world > 1:
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-    ms_max = float(t.item())
-    value = world * verts / (ms_max / 1e3)
+    ms_max, value = replica_throughput(ms, verts, world, dev)
 
     # ---- end to end: pinned host inputs in, results back to host ----
     e2e = None
@@ -316,12 +327,9 @@ def run_ours(args):
         torch.cuda.synchronize()
         barrier()
         check_status("e2e")
-        e_ms = ev0.elapsed_time(ev1) / ee
-        t = torch.tensor([e_ms], device=dev, dtype=torch.float64)
-        if world > 1:
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e = {"value": world * verts / (float(t.item()) / 1e3), "unit": "vertices/s",
-               "ms_per_step": float(t.item()), "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h}
+        e_ms, e_value = replica_throughput(ev0.elapsed_time(ev1) / ee, verts, world, dev)
+        e2e = {"value": e_value, "unit": "vertices/s", "ms_per_step": e_ms, "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": d2h}
 
     # ---- rooflines (live trace over the timed region) ----
     peak, peak_kind = measured_peaks()
