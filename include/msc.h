@@ -24,8 +24,9 @@
  *    not MSC_OK.  No device error traps or hangs the GPU: every device loop
  *    is bounded.
  *  - Workspace: a device buffer of at least msc_workspace_bytes(op, n, nnz)
- *    bytes, 256-byte aligned; its contents on entry do not matter and are
- *    clobbered.
+ *    bytes, 256-byte aligned (a misaligned one returns MSC_ERR_ARG); its
+ *    contents on entry do not matter and are clobbered.  Input and output
+ *    arrays need only their element alignment.
  *  - Vertex ids of a regular grid are linear, x fastest:
  *    v = x + nx * (y + ny * z).  Sizes are limited to n < 2^31 vertices.
  *  - Outputs are deterministic: identical inputs give identical bytes.

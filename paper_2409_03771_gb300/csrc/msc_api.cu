@@ -73,6 +73,10 @@ namespace {
 
 constexpr size_t kCommonWords = 64;  // uint32 control words shared by all stages
 
+// Workspaces are carved into 256-byte aligned pieces, some read with
+// 16-byte loads: the base must be 256-byte aligned.
+bool ws_aligned(const void* ws) { return ((uintptr_t)ws & 255) == 0; }
+
 bool grid_ok(msc_grid g) {
     if (g.nx <= 0 || g.ny <= 0 || g.nz <= 0) return false;
     return (int64_t)g.nx * g.ny * g.nz <= (int64_t)INT32_MAX;
@@ -142,7 +146,8 @@ size_t msc_workspace_bytes(int op, int64_t n, int64_t nnz) {
 
 int msc_order(const float* f, int64_t n, int32_t* order, void* ws, size_t ws_bytes, int32_t* d_status,
               void* stream) {
-    if (n < 0 || n > INT32_MAX || !d_status || (n > 0 && (!f || !order || !ws))) return MSC_ERR_ARG;
+    if (n < 0 || n > INT32_MAX || !d_status || (n > 0 && (!f || !order || !ws || !ws_aligned(ws))))
+        return MSC_ERR_ARG;
     if (ws_bytes < msc_workspace_bytes(MSC_OP_ORDER, n, 0)) return MSC_ERR_WS;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
@@ -170,7 +175,7 @@ int msc_steepest_csr(const int32_t* order, const int32_t* row, const int32_t* co
 }
 
 int msc_compress(int32_t* ptr, int32_t n, void* ws, size_t ws_bytes, int32_t* d_status, void* stream) {
-    if (n < 0 || !d_status || (n > 0 && (!ptr || !ws))) return MSC_ERR_ARG;
+    if (n < 0 || !d_status || (n > 0 && (!ptr || !ws || !ws_aligned(ws)))) return MSC_ERR_ARG;
     if (ws_bytes < msc_workspace_bytes(MSC_OP_COMPRESS, n, 0)) return MSC_ERR_WS;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
@@ -183,7 +188,8 @@ int msc_compress(int32_t* ptr, int32_t n, void* ws, size_t ws_bytes, int32_t* d_
 
 int msc_ms_id(const int32_t* asc, const int32_t* desc, int32_t n, int32_t* ms, int32_t* num_cells,
               void* ws, size_t ws_bytes, int32_t* d_status, void* stream) {
-    if (n < 0 || !d_status || !num_cells || (n > 0 && (!asc || !desc || !ms || !ws))) return MSC_ERR_ARG;
+    if (n < 0 || !d_status || !num_cells || (n > 0 && (!asc || !desc || !ms || !ws || !ws_aligned(ws))))
+        return MSC_ERR_ARG;
     if (ws_bytes < msc_workspace_bytes(MSC_OP_MS_ID, n, 0)) return MSC_ERR_WS;
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
@@ -194,7 +200,7 @@ int msc_ms_id(const int32_t* asc, const int32_t* desc, int32_t n, int32_t* ms, i
 
 int msc_segment(const float* f, msc_grid g, int32_t* order, int32_t* asc, int32_t* desc, int32_t* ms,
                 int32_t* num_cells, void* ws, size_t ws_bytes, int32_t* d_status, void* stream) {
-    if (!grid_ok(g) || !f || !order || !asc || !desc || !ms || !num_cells || !ws || !d_status)
+    if (!grid_ok(g) || !f || !order || !asc || !desc || !ms || !num_cells || !ws || !d_status || !ws_aligned(ws))
         return MSC_ERR_ARG;
     const int64_t n = grid_n(g);
     if (ws_bytes < segment_bytes(n)) return MSC_ERR_WS;

@@ -622,7 +622,9 @@ __global__ void __launch_bounds__(1024) k_pair_scatter_local(const int32_t* __re
             slice[off] = (int32_t)p;
         }
         __syncthreads();
-        const int full = cnt >> 2;
+        // 16-byte stores when the caller's array allows them (s0 is a multiple
+        // of 2^15, so the base pointer decides), else one word at a time
+        const int full = ((uintptr_t)order & 15) == 0 ? cnt >> 2 : 0;
         for (int i = threadIdx.x; i < full; i += 1024)
             reinterpret_cast<int4*>(order + s0)[i] = reinterpret_cast<const int4*>(slice)[i];
         for (int i = full * 4 + threadIdx.x; i < cnt; i += 1024) order[s0 + i] = slice[i];

@@ -359,3 +359,36 @@ def test_cc_mesh_large(m, oracle_mod):
     row, col = workloads.tet_mesh_csr(edge=96, delete_frac=0.55, seed=24)
     got = host(m.cc_mesh(row.cuda(), col.cuda()))
     np.testing.assert_array_equal(got, oracle_mod.cc_csr(row.numpy(), col.numpy()))
+
+
+# ---------------------------------------------------------------------------
+# caller buffers at any 4-byte alignment (views into larger arrays)
+
+
+@pytest.mark.parametrize("shift", [1, 2, 3])
+def test_outputs_at_unaligned_addresses(m, oracle_mod, shift):
+    """Every output pointer offset by 1-3 elements from a 16-byte boundary:
+    the vector paths must fall back, and the results stay exact."""
+    dims = (36, 20, 17)
+    n = dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(shift)
+    f = rng.random(n, dtype=np.float32)
+    fbuf = torch.zeros(n + shift, device="cuda")
+    fbuf[shift:] = cuda(f)
+    bufs = [torch.full((n + shift,), -7, dtype=torch.int32, device="cuda") for _ in range(4)]
+    outs = [b[shift:] for b in bufs]
+    k = torch.zeros(shift + 1, dtype=torch.int32, device="cuda")[shift:]
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    ws = torch.empty(m.msc_workspace_bytes(m.OP_SEGMENT, n), dtype=torch.uint8, device="cuda")
+    assert m.msc_segment(fbuf[shift:], dims, *outs, k, ws, ws.numel(), st) == m.OK
+    torch.cuda.synchronize()
+    assert int(st.item()) == m.OK
+    wo, wa, wd, wm, wk = oracle_mod.segment_grid(f, dims)
+    for got, want in zip(outs, (wo, wa, wd, wm)):
+        np.testing.assert_array_equal(host(got), want)
+    assert int(k.item()) == wk
+    # the order alone, into an unaligned view as well
+    ows = torch.empty(m.msc_workspace_bytes(m.OP_ORDER, n), dtype=torch.uint8, device="cuda")
+    obuf = torch.full((n + shift,), -7, dtype=torch.int32, device="cuda")
+    assert m.msc_order(fbuf[shift:], n, obuf[shift:], ows, ows.numel(), st) == m.OK
+    np.testing.assert_array_equal(host(obuf[shift:]), wo)

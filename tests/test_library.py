@@ -59,8 +59,11 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert m.msc_steepest_grid(0, (4, 4, 4), 0, 0, stream=0) == m.ERR_ARG
     assert m.msc_steepest_grid(16, (0, 4, 4), 16, 16, stream=0) == m.ERR_ARG
     assert m.msc_cc_mask(16, (4, 4, 4), 7, 16, 16, 256, 16, stream=0) == m.ERR_ARG
-    assert m.msc_segment(16, (4, 4, 4), 16, 16, 16, 16, 16, 16, 10, 16, stream=0) == m.ERR_WS
-    assert m.msc_compress(16, 10, 16, 0, 16, stream=0) == m.ERR_WS
+    assert m.msc_segment(16, (4, 4, 4), 16, 16, 16, 16, 16, 256, 10, 16, stream=0) == m.ERR_WS
+    assert m.msc_compress(16, 10, 256, 0, 16, stream=0) == m.ERR_WS
+    # a workspace that is not 256-byte aligned is refused before any launch
+    assert m.msc_compress(16, 10, 16 + 4, 1 << 20, 16, stream=0) == m.ERR_ARG
+    assert m.msc_order(16, 10, 16, 256 + 16, 1 << 30, 16, stream=0) == m.ERR_ARG
     # the batch and serving entry points check their arguments on the host too
     assert m.msc_batch_workspace_bytes([(4, 4, 4), (2, 3, 5)]) > m.msc_batch_workspace_bytes([(4, 4, 4)]) > 0
     assert m.msc_batch_workspace_bytes([(4, 4, 0)]) == 0
