@@ -47,6 +47,7 @@ def parse_args():
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-serve", action="store_true", help="skip the served-request rate sweep")
     ap.add_argument("--serve-requests", type=int, default=64, help="requests per arrival rate")
+    ap.add_argument("--no-density", action="store_true", help="skip the 1024^3 mask-density sweep")
     return ap.parse_args()
 
 
@@ -425,6 +426,9 @@ def run_ours(args):
     if not args.no_serve:
         torch.cuda.empty_cache()
         out["serve"] = serve_bench(dev, args.serve_requests)
+    if not args.no_density:
+        torch.cuda.empty_cache()
+        out["cc_density"] = density_bench(dev)
     if rank == 0:
         print(json.dumps(out), flush=True)
     if world > 1:
@@ -595,6 +599,45 @@ def serve_bench(dev, count):
         "latency": "host submit to completion seen by the server (completion callback)",
         "rates": rates, "input_gen_s": round(gen_s, 1), "clocks": clk.summary(),
     }
+
+
+# ---------------------------------------------------------------------------
+# connected components across mask densities (the paper's top 10 / 50 / 90 %
+# sweep at 1024^3), with 6 and with the triangulation's 14 neighbours
+
+
+def density_bench(dev, edge=1024, reps=3):
+    import torch
+
+    import paper_2409_03771_gb300 as msc
+    import workloads
+
+    n = edge ** 3
+    lab = torch.empty(n, dtype=torch.int32, device=dev)
+    ws = torch.empty(256, dtype=torch.uint8, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    rows = []
+    for top in (0.1, 0.5, 0.9):
+        mask = workloads.mask_top(edge=edge, seed=2, top=top, device=dev).reshape(-1)
+        frac = float(mask.float().mean().item())
+        for conn in (6, 14):
+            for _ in range(2):
+                assert msc.msc_cc_mask(mask, (edge,) * 3, conn, lab, ws, 256, st, stream) == 0
+            ev0.record(stream)
+            for _ in range(reps):
+                assert msc.msc_cc_mask(mask, (edge,) * 3, conn, lab, ws, 256, st, stream) == 0
+            ev1.record(stream)
+            torch.cuda.synchronize()
+            if int(st.item()) != 0:
+                raise RuntimeError(f"cc_mask at top {top}, conn {conn}: device status {int(st.item())}")
+            ms = ev0.elapsed_time(ev1) / reps
+            rows.append({"top": top, "mask_fraction": round(frac, 4), "conn": conn, "ms": round(ms, 3),
+                         "vertices_per_s": n / (ms / 1e3)})
+        del mask
+    return {"workload": f"CC of the top 10/50/90 % of a {edge}^3 field of 256 Gaussians (seed 2)",
+            "rows": rows}
 
 
 # ---------------------------------------------------------------------------

@@ -108,11 +108,15 @@ def test_segment_512_sampled_and_properties(m, oracle_mod, kind):
         assert oracle_mod.order_at(fh, int(v)) == int(order[int(v)])
 
 
-def test_cc_mask_1024_properties_and_samples(m, oracle_mod):
-    E = 1024
+POS6 = [(1, 0, 0), (0, 1, 0), (0, 0, 1)]
+POS14 = POS6 + [(1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+
+
+def check_cc(m, oracle_mod, mask, E, conn):
+    """Properties that pin min-id component labels, plus BFS on the three
+    smallest components."""
     dims = (E, E, E)
-    mask = workloads.mask_blobs(edge=E, seed=2, device="cuda").reshape(-1)
-    lab = m.cc_mask(mask, dims, 6)
+    lab = m.cc_mask(mask, dims, conn)
     n = mask.numel()
     on = mask != 0
     assert bool(((lab == -1) == ~on).all())
@@ -122,24 +126,35 @@ def test_cc_mask_1024_properties_and_samples(m, oracle_mod):
     assert bool((lab[l[on]] == lab[on]).all())
     L = lab.reshape(E, E, E)
     M = on.reshape(E, E, E)
-    for dim in range(3):
-        a = [slice(None)] * 3
-        b = [slice(None)] * 3
-        a[dim] = slice(0, E - 1)
-        b[dim] = slice(1, E)
-        both = M[tuple(a)] & M[tuple(b)]
-        assert bool((L[tuple(a)][both] == L[tuple(b)][both]).all()), f"label changes across axis {dim}"
-    # the three smallest components against BFS from one of their vertices
+    for dx, dy, dz in (POS6 if conn == 6 else POS14):
+        a = (slice(0, E - dz), slice(0, E - dy), slice(0, E - dx))
+        b = (slice(dz, E), slice(dy, E), slice(dx, E))
+        both = M[a] & M[b]
+        assert bool((L[a][both] == L[b][both]).all()), f"label changes across offset {(dx, dy, dz)}"
     sizes = torch.bincount(l[on], minlength=n)
     roots = torch.nonzero(sizes).reshape(-1)
     small = roots[torch.argsort(sizes[roots])[:3]].cpu().numpy()
     del L, M, l, ids, sizes, roots
-    mh = mask.cpu().numpy()
+    mh = mask.reshape(-1).cpu().numpy()
     rng = np.random.default_rng(3)
     for root in small:
         members = torch.nonzero(lab == int(root)).reshape(-1)
         v = int(members[int(rng.integers(0, members.numel()))])
-        assert oracle_mod.cc_grid_at(mh, dims, 6, v) == (int(root), members.numel())  # (min id, size)
+        assert oracle_mod.cc_grid_at(mh, dims, conn, v) == (int(root), members.numel())  # (min id, size)
+
+
+def test_cc_mask_1024_properties_and_samples(m, oracle_mod):
+    mask = workloads.mask_blobs(edge=1024, seed=2, device="cuda").reshape(-1)
+    check_cc(m, oracle_mod, mask, 1024, 6)
+
+
+@pytest.mark.parametrize("top,conn", [(0.1, 14), (0.9, 14), (0.5, 6)])
+def test_cc_density_sweep_1024(m, oracle_mod, top, conn):
+    """The paper's mask-density sweep (top 10 / 50 / 90 % of the field) at
+    1024^3, with the triangulation's 14-neighbour link and with 6."""
+    mask = workloads.mask_top(edge=1024, seed=2, top=top, device="cuda").reshape(-1)
+    assert abs(float(mask.float().mean()) - top) < 0.005
+    check_cc(m, oracle_mod, mask, 1024, conn)
 
 
 def test_cc_mesh_256_full_oracle(m, oracle_mod):

@@ -106,6 +106,19 @@ def mask_blobs(edge=1024, seed=2, device="cpu", threshold=0.3):
     return feature_mask((edge,) * 3, 256, (0.5 * s, 1.5 * s), threshold, seed, device=device)
 
 
+def mask_top(edge=1024, seed=2, top=0.1, device="cpu", sample=1 << 22):
+    """The feature mask of the paper's density sweep: the voxels holding the
+    top `top` fraction of the blob field's values (the mask_blobs field).
+    The threshold is the (1 - top) quantile of a seeded sample of 2^22
+    voxels, so the masked fraction is `top` to within about a thousandth."""
+    s = edge / 1024.0 * 128.0
+    f = smooth_field((edge,) * 3, 256, (0.5 * s, 1.5 * s), seed, device=device).reshape(-1)
+    g = torch.Generator(device=f.device).manual_seed(seed)
+    idx = torch.randint(0, f.numel(), (min(sample, f.numel()),), device=f.device, generator=g)
+    thr = torch.quantile(f[idx].double(), 1.0 - top).item()
+    return (f > thr).to(torch.uint8).reshape((edge,) * 3)
+
+
 # ----------------------------------------------------------------------------
 # tetrahedral mesh
 
