@@ -68,6 +68,7 @@ def _load():
             "oracle_cc_grid": (i32, [P, i32, i32, i32, i32, P]),
             "oracle_cc_csr": (i32, [P, P, i32, P]),
             "oracle_cc_grid_at": (i32, [P, i32, i32, i32, i32, i64, P, P]),
+            "oracle_adjacency_grid": (i32, [P, i32, i32, i32, i32, P, P, i64, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -217,3 +218,18 @@ def cc_grid_at(mask, dims, conn: int, v: int):
         "cc_grid_at",
     )
     return mn.value, sz.value
+
+
+def adjacency_grid(label, dims, conn: int = 14):
+    """Distinct pairs (a, b), a < b, of different non-negative labels joined by
+    an edge of the triangulation (conn 14) or of the face grid (conn 6),
+    sorted: two int32 arrays."""
+    nx, ny, nz = dims
+    lab = _c(label, np.int32).ravel()
+    cnt = ctypes.c_int64()
+    _check(_load().oracle_adjacency_grid(_ptr(lab), nx, ny, nz, conn, 0, 0, 0, ctypes.byref(cnt)), "adjacency_grid")
+    a = np.empty(max(cnt.value, 1), np.int32)
+    b = np.empty(max(cnt.value, 1), np.int32)
+    _check(_load().oracle_adjacency_grid(_ptr(lab), nx, ny, nz, conn, _ptr(a), _ptr(b), cnt.value,
+                                         ctypes.byref(cnt)), "adjacency_grid")
+    return a[:cnt.value], b[:cnt.value]

@@ -487,3 +487,65 @@ int32_t oracle_cc_grid_at(const uint8_t* mask, int32_t nx, int32_t ny,
     *size = count;
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Adjacency of labelled regions (the preview of the Morse-Smale complex
+ * assembled from the segmentations, Related Work; the extremum graph named
+ * as future work in the Conclusion): every edge (u, v) of the implicit
+ * triangulation (conn 14) or of the face grid (conn 6) whose endpoints carry
+ * two different non-negative labels contributes the pair (min, max) of the
+ * two labels.  Output: the distinct pairs in lexicographic order, written to
+ * a_out / b_out (caller-provided, cap entries) and counted in *count.  When
+ * more than cap distinct pairs exist, *count holds their number and nothing
+ * beyond cap is written.                                                    */
+
+static int or_cmp_u64(const void* x, const void* y) {
+    const uint64_t a = *(const uint64_t*)x, b = *(const uint64_t*)y;
+    return a < b ? -1 : a > b;
+}
+
+int oracle_adjacency_grid(const int32_t* label, int32_t nx, int32_t ny, int32_t nz, int conn,
+                          int32_t* a_out, int32_t* b_out, int64_t cap, int64_t* count) {
+    if (!or_grid_ok(nx, ny, nz) || !label || !count || (conn != 6 && conn != 14) || cap < 0) return OR_ERR_ARG;
+    const int (*off)[3] = conn == 6 ? OR_FACE6 : OR_FREUD;
+    const int64_t n = (int64_t)nx * ny * nz;
+    /* every edge once: only the offsets that come first in the table of each
+     * +- pair (the even entries) are followed from each vertex */
+    int64_t m = 0, mcap = 1024;
+    uint64_t* pairs = (uint64_t*)malloc((size_t)mcap * sizeof(uint64_t));
+    if (!pairs) return OR_ERR_OOM;
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t x = v % nx, y = (v / nx) % ny, z = v / ((int64_t)nx * ny);
+        for (int k = 0; k < conn; k += 2) {
+            const int64_t xx = x + off[k][0], yy = y + off[k][1], zz = z + off[k][2];
+            if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz) continue;
+            const int64_t u = xx + (int64_t)nx * (yy + (int64_t)ny * zz);
+            const int32_t a = label[v], b = label[u];
+            if (a < 0 || b < 0 || a == b) continue;
+            if (m == mcap) {
+                mcap *= 2;
+                uint64_t* p2 = (uint64_t*)realloc(pairs, (size_t)mcap * sizeof(uint64_t));
+                if (!p2) {
+                    free(pairs);
+                    return OR_ERR_OOM;
+                }
+                pairs = p2;
+            }
+            const uint32_t lo = (uint32_t)(a < b ? a : b), hi = (uint32_t)(a < b ? b : a);
+            pairs[m++] = ((uint64_t)lo << 32) | hi;
+        }
+    }
+    qsort(pairs, (size_t)m, sizeof(uint64_t), or_cmp_u64);
+    int64_t k = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        if (i > 0 && pairs[i] == pairs[i - 1]) continue;
+        if (k < cap) {
+            a_out[k] = (int32_t)(pairs[i] >> 32);
+            b_out[k] = (int32_t)(uint32_t)pairs[i];
+        }
+        ++k;
+    }
+    free(pairs);
+    *count = k;
+    return OR_OK;
+}
