@@ -70,7 +70,8 @@ enum {
     MSC_OP_MS_ID = 3,
     MSC_OP_SEGMENT = 4,
     MSC_OP_CC_MASK = 5,
-    MSC_OP_CC_MESH = 6
+    MSC_OP_CC_MESH = 6,
+    MSC_OP_ADJACENCY = 7
 };
 
 /* Workspace bytes needed by `op` on n vertices (nnz CSR entries for
@@ -193,6 +194,35 @@ MSC_API int msc_cc_mask(const uint8_t* mask, msc_grid g, int32_t conn, int32_t* 
  * with its root. */
 MSC_API int msc_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* label, void* ws,
                 size_t ws_bytes, int32_t* d_status, void* stream);
+
+/* Adjacency of labelled regions: the connectivity preview of the
+ * Morse-Smale complex built from its segmentations (section "Related Work",
+ * Morse-Smale Complex) and the arcs of an extremum graph (Conclusion).  The
+ * paper names both without defining an operation; this one is: every edge
+ * (u, v) of the grid whose ends carry two different non-negative labels
+ * gives the pair (min, max) of the two labels, and the result is the set of
+ * distinct pairs in lexicographic order.  With asc or desc labels the pairs
+ * are the minima or maxima whose manifolds touch; with cell ids, the cells
+ * that share a boundary.
+ *   label      device int32[n]: a label per vertex, negative = unlabelled.
+ *   conn       14: the edges of the implicit triangulation (offsets
+ *              (1,0,0), (0,1,0), (0,0,1), (1,1,0), (1,0,1), (0,1,1),
+ *              (1,1,1)); 6: the face grid (the first three).
+ *   label_bound  every label is below it (n for vertex-id labels, the cell
+ *              count for cell ids; 1 .. 2^31-1).  A label at or above it
+ *              sets MSC_ERR_ARG in d_status.  A tighter bound sorts fewer
+ *              key bits: the pair key is lo * 2^s + hi, s = ceil(log2 bound).
+ *   a, b       device int32[cap] out: the first min(cap, K) pairs, a < b.
+ *   num_pairs  device int64 out: K, the number of distinct pairs (it may
+ *              exceed cap; nothing is written past cap).
+ * Workspace: msc_workspace_bytes(MSC_OP_ADJACENCY, n, 0), sized for 7n pair
+ * keys (every edge of the 14-neighbour triangulation); n above
+ * (2^31 - 1) / 7 returns MSC_ERR_TOO_LARGE.
+ * Method: tiles of the grid, each de-duplicating its pair keys in a shared
+ * hash set; radix sort of the tiles' keys; first key of every run. */
+MSC_API int msc_adjacency_grid(const int32_t* label, msc_grid g, int32_t conn, int32_t label_bound,
+                               int32_t* a, int32_t* b, int64_t cap, int64_t* num_pairs, void* ws,
+                               size_t ws_bytes, int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------
  * Batched segmentation.  The paper segments one grid at a time; a batch

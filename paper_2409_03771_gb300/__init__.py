@@ -35,13 +35,14 @@ __all__ = [
     "msc_batch_plan_kernels", "msc_batch_plan_destroy", "msc_batch_autotune", "Batch",
     "Job", "Result", "JOB_SEGMENT", "JOB_CC_MASK", "msc_server_create", "msc_server_submit", "msc_server_poll",
     "msc_server_wait", "msc_server_release", "msc_server_stats", "msc_server_destroy", "Server",
+    "OP_ADJACENCY", "msc_adjacency_grid", "adjacency_grid",
 ]
 
 OK, ERR_ARG, ERR_WS, ERR_CUDA, ERR_NAN, ERR_NOT_CONVERGED, ERR_BUDGET, ERR_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
 ERR_TOO_LARGE = -8
 NOALLOC_MAX_N = 1 << 22
 PENDING = 1
-OP_ORDER, OP_COMPRESS, OP_MS_ID, OP_SEGMENT, OP_CC_MASK, OP_CC_MESH = 1, 2, 3, 4, 5, 6
+OP_ORDER, OP_COMPRESS, OP_MS_ID, OP_SEGMENT, OP_CC_MASK, OP_CC_MESH, OP_ADJACENCY = 1, 2, 3, 4, 5, 6, 7
 JOB_SEGMENT, JOB_CC_MASK = 1, 2
 
 
@@ -103,6 +104,7 @@ def load(build_if_missing: bool = False):
         "msc_segment": (ctypes.c_int, [P, Grid, P, P, P, P, P, P, SZ, P, P]),
         "msc_cc_mask": (ctypes.c_int, [P, Grid, I32, P, P, SZ, P, P]),
         "msc_cc_mesh": (ctypes.c_int, [P, P, I32, P, P, SZ, P, P]),
+        "msc_adjacency_grid": (ctypes.c_int, [P, Grid, I32, I32, P, P, I64, P, P, SZ, P, P]),
         "msc_launch_count": (ctypes.c_ulonglong, []),
         "msc_trace_enable": (None, [ctypes.c_int]),
         "msc_trace_reset": (None, []),
@@ -208,6 +210,12 @@ def msc_cc_mask(mask, dims, conn, label, ws, ws_bytes, status, stream=None) -> i
 
 def msc_cc_mesh(row, col, n, label, ws, ws_bytes, status, stream=None) -> int:
     return load().msc_cc_mesh(_p(row), _p(col), n, _p(label), _p(ws), ws_bytes, _p(status), _stream(stream))
+
+
+def msc_adjacency_grid(label, dims, conn, label_bound, a, b, cap, num_pairs, ws, ws_bytes, status,
+                       stream=None) -> int:
+    return load().msc_adjacency_grid(_p(label), _grid(dims), conn, label_bound, _p(a), _p(b), cap, _p(num_pairs),
+                                     _p(ws), ws_bytes, _p(status), _stream(stream))
 
 
 def msc_launch_count() -> int:
@@ -436,6 +444,36 @@ def cc_mesh(row: torch.Tensor, col: torch.Tensor) -> torch.Tensor:
     _check(msc_cc_mesh(row, col, n, lab, ws, ws.numel(), st), "msc_cc_mesh")
     _finish(st, "msc_cc_mesh")
     return lab
+
+
+def adjacency_grid(label: torch.Tensor, dims, conn: int = 14, label_bound: int | None = None,
+                   cap: int | None = None, ws: torch.Tensor | None = None):
+    """Distinct pairs (a, b), a < b, of different non-negative labels that
+    meet across an edge of the grid (conn 14: the triangulation, 6: the face
+    grid), in lexicographic order, as two int32 tensors.  label_bound
+    (default n) bounds every label.  The pairs are first collected into
+    `cap` slots (default min(7n, 2^24)); a call that finds more runs again
+    with room for all of them."""
+    dev = _dev(label)
+    lab = _flat(label, torch.int32)
+    n = lab.numel()
+    if n != int(dims[0]) * int(dims[1]) * int(dims[2]):
+        raise MSCError(ERR_ARG, "adjacency_grid: dims do not match the label size")
+    bound = max(n, 1) if label_bound is None else int(label_bound)
+    cap = min(7 * n, 1 << 24) if cap is None else int(cap)
+    if ws is None:
+        ws = _ws(OP_ADJACENCY, n, dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    k = torch.empty(1, dtype=torch.int64, device=dev)
+    while True:
+        a = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        b = torch.empty(max(cap, 1), dtype=torch.int32, device=dev)
+        _check(msc_adjacency_grid(lab, dims, conn, bound, a, b, cap, k, ws, ws.numel(), st), "msc_adjacency_grid")
+        _finish(st, "msc_adjacency_grid")
+        K = int(k.item())
+        if K <= cap:
+            return a[:K], b[:K]
+        cap = K
 
 
 class Batch:

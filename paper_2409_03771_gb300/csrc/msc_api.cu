@@ -6,6 +6,7 @@
 #include <algorithm>
 #include <mutex>
 
+#include "adjacency.cuh"
 #include "cc.cuh"
 #include "common.cuh"
 #include "compress.cuh"
@@ -121,7 +122,7 @@ const char* msc_status_string(int code) {
         case MSC_ERR_NOT_CONVERGED: return "pointer jumping did not converge (pointer cycle)";
         case MSC_ERR_BUDGET: return "request exceeds the memory budget";
         case MSC_ERR_INTERNAL: return "internal error";
-        case MSC_ERR_TOO_LARGE: return "size exceeds the static scratch of the no-allocation entry point";
+        case MSC_ERR_TOO_LARGE: return "size exceeds a limit of the entry point";
         case MSC_PENDING: return "pending";
         default: return "unknown status";
     }
@@ -140,6 +141,10 @@ size_t msc_workspace_bytes(int op, int64_t n, int64_t nnz) {
         case MSC_OP_SEGMENT: return segment_bytes(n);
         case MSC_OP_CC_MASK: return 256;
         case MSC_OP_CC_MESH: return 256;
+        case MSC_OP_ADJACENCY:
+            if (!adjacency_size_ok(n)) return 0;
+            size_adjacency_scratch(s, n);
+            return s.used;
         default: return 0;
     }
 }
@@ -264,6 +269,20 @@ int msc_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* labe
     MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
     if (n == 0) return MSC_OK;
     return run_cc_mesh(row, col, n, label, d_status, s, static_cast<int32_t*>(ws));
+}
+
+int msc_adjacency_grid(const int32_t* label, msc_grid g, int32_t conn, int32_t label_bound, int32_t* a,
+                       int32_t* b, int64_t cap, int64_t* num_pairs, void* ws, size_t ws_bytes,
+                       int32_t* d_status, void* stream) {
+    if (!grid_ok(g) || !label || !num_pairs || !d_status || !ws || !ws_aligned(ws) ||
+        (conn != 6 && conn != 14) || label_bound <= 0 || cap < 0 || (cap > 0 && (!a || !b)))
+        return MSC_ERR_ARG;
+    const int64_t n = grid_n(g);
+    if (!adjacency_size_ok(n)) return MSC_ERR_TOO_LARGE;
+    if (ws_bytes < msc_workspace_bytes(MSC_OP_ADJACENCY, n, 0)) return MSC_ERR_WS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
+    return run_adjacency_grid(label, g, conn, label_bound, a, b, cap, num_pairs, ws, ws_bytes, d_status, s);
 }
 
 }  // extern "C"

@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(256) k_hist(const KeyT* __restrict__ keys,
     for (int i = tid; i < kWarps * npass * kBins; i += blockDim.x) sh[i] = 0;
     __syncthreads();
     uint32_t* wsh = sh + warp * npass * kBins;
-    const int64_t n = d_n ? (int64_t)*d_n : n_host;
+    const int64_t n = d_n ? min((int64_t)*d_n, n_host) : n_host;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x * kHistRun;
     bool saw_nan = false;
     for (int64_t i0 = ((int64_t)blockIdx.x * blockDim.x + tid) * kHistRun; i0 < n; i0 += stride) {
@@ -303,7 +303,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
     int32_t* s_vals = reinterpret_cast<int32_t*>(s_keys + kSortTile);
 
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int64_t n_all = a.d_n ? (int64_t)*a.d_n : a.n;
+    const int64_t n_all = a.d_n ? min((int64_t)*a.d_n, a.n) : a.n;  // a device count never exceeds the buffers
     const int64_t ntiles = SEG ? a.seg_tiles : (n_all + kSortTile - 1) / kSortTile;
     if constexpr (!SEG) {
         const uint32_t c = a.hist[tid];
@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
         uint32_t rk[kItems];  // (digit << 16) | rank among the warp's equal digits
         {
             const KeyT* kin = FROM_F ? nullptr : a.keys_in + tbase;
-            const int32_t* vin = FROM_F ? nullptr : a.vals_in + tbase;
+            const int32_t* vin = FROM_F || !a.vals_in ? nullptr : a.vals_in + tbase;  // keys only: no payload
             const float* fin = FROM_F ? a.f_in + tbase : nullptr;
 #pragma unroll
             for (int k = 0; k < kItems; ++k) {
@@ -346,7 +346,7 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
                         val[k] = (int32_t)tbase + li;
                     } else {
                         key[k] = kin[li];
-                        val[k] = vin[li];
+                        val[k] = vin ? vin[li] : 0;
                     }
                 } else {
                     key[k] = 0;
@@ -495,14 +495,14 @@ __global__ void __launch_bounds__(kThreads, 3) k_onesweep(const PassArgs<KeyT> a
                 }
             } else {
                 KeyT* kout = a.keys_out + seg_base;
-                int32_t* vout = a.vals_out + seg_base;
+                int32_t* vout = a.vals_out ? a.vals_out + seg_base : nullptr;
                 for (int i = tid; i < cnt; i += kThreads) {
                     const KeyT kk = s_keys[i];
                     const uint32_t d = (uint32_t)(kk >> a.shift) & 255u;
                     const uint32_t pos = s_gbase[d] + (uint32_t)i - s_excl[d];
                     MSC_GUARD(pos < (uint64_t)n, a.status, -102) {
                         kout[pos] = kk;
-                        vout[pos] = s_vals[i];
+                        if (vout) vout[pos] = s_vals[i];
                     }
                 }
             }
@@ -704,6 +704,16 @@ static int clear_scratch(const SortScratch& sc, int64_t n, cudaStream_t s) {
     return MSC_OK;
 }
 
+// Clears the look-back words of the tiles that *d_n keys occupy (a sort
+// whose count is known only on the device touches no other tile).
+__global__ void k_clear_lookback(unsigned long long* lookback, const int32_t* __restrict__ d_n,
+                                 int64_t max_n) {
+    const int64_t words = ((min((int64_t)*d_n, max_n) + kSortTile - 1) / kSortTile) * kBins;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < words;
+         i += (int64_t)gridDim.x * blockDim.x)
+        lookback[i] = 0ull;
+}
+
 static size_t hist_smem(int npass) { return (size_t)kWarps * npass * kBins * sizeof(uint32_t); }
 
 // Allow both histogram kernels the shared memory of 8 passes (64 KiB).
@@ -875,15 +885,23 @@ int run_order_seg(const float* f, const SegTable& t, int32_t* order, uint32_t* k
 
 int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* keys_alt,
                  int32_t* vals_alt, const int32_t* d_count, int64_t max_count, int key_bits,
-                 const SortScratch& sc, int32_t* status, cudaStream_t s, bool* result_in_alt) {
+                 const SortScratch& sc, int32_t* status, cudaStream_t s, bool* result_in_alt,
+                 const char* hist_label, const char* pass_label) {
     *result_in_alt = false;
     if (max_count <= 0 || key_bits <= 0) return MSC_OK;
     const int npass = std::min(8, (key_bits + 7) / 8);
-    int r = clear_scratch(sc, max_count, s);
-    if (r) return r;
-    if ((r = configure_hist())) return r;
+    MSC_TRY(cudaMemsetAsync(sc.hist, 0, (8 * kBins + kCounterWords) * sizeof(uint32_t), s));
     {
-        TraceScope ts_("msid.sort_hist", s);
+        TraceScope ts_("sort.clear_lookback", s);
+        k_clear_lookback<<<(unsigned)std::min<int64_t>(ceil_div(ceil_div(max_count, kSortTile) * kBins, 256),
+                                                       (int64_t)current_device().sms * 8),
+                           256, 0, s>>>(sc.lookback, d_count, max_count);
+    }
+    MSC_LAUNCHED();
+    int r = configure_hist();
+    if (r) return r;
+    {
+        TraceScope ts_(hist_label, s);
         k_hist<unsigned long long, false><<<hist_grid(max_count), 256, hist_smem(npass), s>>>(keys, nullptr, max_count, d_count, npass, sc.hist, status);
     }
     MSC_LAUNCHED();
@@ -905,7 +923,7 @@ int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* ke
         a.shift = 8 * p;
         a.tile_counter = sc.tile_counters + p;
         a.epoch = (uint32_t)(p + 1);
-        if ((r = launch_pass<unsigned long long, false, false>(a, max_count, s, "msid.sort_pass"))) return r;
+        if ((r = launch_pass<unsigned long long, false, false>(a, max_count, s, pass_label))) return r;
         std::swap(kin, kout);
         std::swap(vin, vout);
     }

@@ -50,9 +50,11 @@ int run_order_seg(const float* f, const SegTable& t, int32_t* order, uint32_t* k
 
 // Stable sort of (keys, vals) by the low `key_bits` bits of keys.  The
 // count is read on the device from *d_count (<= max_count).  Returns, via
-// *result_in_alt, whether the sorted data ended in the alt buffers.
+// *result_in_alt, whether the sorted data ended in the alt buffers.  With
+// vals and vals_alt both null the keys are sorted alone.
 int run_sort_u64(unsigned long long* keys, int32_t* vals, unsigned long long* keys_alt,
                  int32_t* vals_alt, const int32_t* d_count, int64_t max_count, int key_bits,
-                 const SortScratch& sc, int32_t* status, cudaStream_t s, bool* result_in_alt);
+                 const SortScratch& sc, int32_t* status, cudaStream_t s, bool* result_in_alt,
+                 const char* hist_label = "msid.sort_hist", const char* pass_label = "msid.sort_pass");
 
 }  // namespace msc

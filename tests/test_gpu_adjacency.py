@@ -1,0 +1,182 @@
+"""Region adjacency on the GPU (msc_adjacency_grid) against the oracle:
+random labels on grids that span several 32 x 8 x 4 tiles with ragged
+tails, every edge of the grid (labels = vertex ids), the minimum / maximum
+labels and cell ids of segmentations computed by the oracle, component
+labels, thin grids, truncation at the capacity and the error cases.  At the
+full size the result is compared with plain PyTorch set operations over
+every edge of the grid."""
+import numpy as np
+import pytest
+import torch
+
+import workloads
+
+pytestmark = pytest.mark.gpu
+
+POS = [(1, 0, 0), (0, 1, 0), (0, 0, 1), (1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)]
+
+
+@pytest.fixture(scope="module")
+def m():
+    import paper_2409_03771_gb300 as msc
+    from paper_2409_03771_gb300 import _build
+
+    _build.build()
+    msc.load()
+    return msc
+
+
+def gpu_pairs(m, lab, dims, conn, bound=None):
+    a, b = m.adjacency_grid(torch.as_tensor(lab).cuda(), dims, conn, label_bound=bound)
+    return a.cpu().numpy(), b.cpu().numpy()
+
+
+def check(m, oracle_mod, lab, dims, conn, bound=None):
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    wa, wb = oracle_mod.adjacency_grid(lab, dims, conn)
+    ga, gb = gpu_pairs(m, lab, dims, conn, bound)
+    np.testing.assert_array_equal(ga, wa)
+    np.testing.assert_array_equal(gb, wb)
+    return wa.size
+
+
+@pytest.mark.parametrize("conn", [6, 14])
+@pytest.mark.parametrize("dims", [(70, 19, 11), (33, 9, 5), (31, 7, 3), (96, 40, 9)])
+def test_random_labels(m, oracle_mod, dims, conn):
+    rng = np.random.default_rng(dims[0] + conn)
+    n = dims[0] * dims[1] * dims[2]
+    lab = rng.integers(-1, 40, n).astype(np.int32)
+    k = check(m, oracle_mod, lab, dims, conn, bound=40)
+    assert k > 100
+    check(m, oracle_mod, lab, dims, conn)  # loose bound: wider keys, same pairs
+
+
+@pytest.mark.parametrize("conn", [6, 14])
+def test_every_edge_is_a_pair(m, oracle_mod, conn):
+    dims = (37, 9, 6)
+    n = 37 * 9 * 6
+    k = check(m, oracle_mod, np.arange(n, dtype=np.int32), dims, conn)
+    edges6 = 3 * n - (9 * 6 + 37 * 6 + 37 * 9)
+    assert k == edges6 if conn == 6 else k > 2 * edges6
+
+
+@pytest.mark.parametrize("dims", [(1, 1, 1), (50, 1, 1), (1, 1, 50), (1, 40, 1), (7, 1, 9), (1, 13, 5), (2, 2, 2)])
+def test_thin_grids(m, oracle_mod, dims):
+    n = dims[0] * dims[1] * dims[2]
+    rng = np.random.default_rng(n)
+    for conn in (6, 14):
+        check(m, oracle_mod, rng.integers(-1, 6, n).astype(np.int32), dims, conn, bound=6)
+        check(m, oracle_mod, np.arange(n, dtype=np.int32), dims, conn)
+
+
+def test_constant_and_unlabelled(m):
+    dims = (40, 20, 10)
+    n = 8000
+    for lab in (np.full(n, 5, np.int32), np.full(n, -1, np.int32), np.full(n, -7, np.int32)):
+        for conn in (6, 14):
+            a, b = gpu_pairs(m, lab, dims, conn)
+            assert a.size == 0 and b.size == 0
+
+
+@pytest.mark.parametrize("kind,edge", [("smooth", 64), ("noise", 40)])
+def test_segmentation_labels(m, oracle_mod, kind, edge):
+    """The Morse-Smale preview: pairs of minima, of maxima and of cells that
+    touch, for labels the oracle computed."""
+    dims = (edge, edge + 3, edge - 5)  # ragged against every tile extent
+    n = dims[0] * dims[1] * dims[2]
+    if kind == "smooth":
+        f = workloads.smooth_field(dims, 12, (3.0, 9.0), seed=4).reshape(-1).numpy()
+    else:
+        f = workloads.white_noise(dims, seed=4).reshape(-1).numpy()
+    order, asc, desc, ms, cells = oracle_mod.segment_grid(f, dims)
+    for lab, bound in ((asc, n), (desc, n), (ms, cells)):
+        for conn in (14, 6):
+            k = check(m, oracle_mod, lab, dims, conn, bound=bound)
+            assert k > 0
+
+
+def test_component_labels(m, oracle_mod):
+    """Components of one connectivity never touch under it; under the wider
+    triangulation link, 6-components can meet across diagonals."""
+    dims = (60, 45, 30)
+    mask = workloads.feature_mask(dims, 20, (2.0, 5.0), 0.2, seed=9).reshape(-1).numpy()
+    lab6 = oracle_mod.cc_grid(mask, dims, 6)
+    lab14 = oracle_mod.cc_grid(mask, dims, 14)
+    assert check(m, oracle_mod, lab6, dims, 6) == 0
+    assert check(m, oracle_mod, lab14, dims, 14) == 0
+    check(m, oracle_mod, lab6, dims, 14)
+
+
+def test_capacity_truncates_and_counts(m, oracle_mod):
+    dims = (50, 30, 20)
+    n = 30000
+    lab = np.random.default_rng(1).integers(0, 300, n).astype(np.int32)
+    wa, wb = oracle_mod.adjacency_grid(lab, dims, 14)
+    K = wa.size
+    d = torch.as_tensor(lab).cuda()
+    ws = torch.empty(m.msc_workspace_bytes(m.OP_ADJACENCY, n), dtype=torch.uint8, device="cuda")
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    k = torch.empty(1, dtype=torch.int64, device="cuda")
+    for cap in (0, 1, K // 3, K, K + 5):
+        a = torch.full((cap + 8,), -5, dtype=torch.int32, device="cuda")
+        b = torch.full((cap + 8,), -5, dtype=torch.int32, device="cuda")
+        assert m.msc_adjacency_grid(d, dims, 14, 300, a, b, cap, k, ws, ws.numel(), st) == m.OK
+        torch.cuda.synchronize()
+        assert int(st.item()) == m.OK and int(k.item()) == K
+        c = min(cap, K)
+        np.testing.assert_array_equal(a[:c].cpu().numpy(), wa[:c])
+        np.testing.assert_array_equal(b[:c].cpu().numpy(), wb[:c])
+        assert bool((a[c:] == -5).all()) and bool((b[c:] == -5).all()), "written past the capacity"
+    # the binding grows its buffer when the first capacity is too small
+    a, b = m.adjacency_grid(d, dims, 14, label_bound=300, cap=7)
+    np.testing.assert_array_equal(a.cpu().numpy(), wa)
+
+
+def test_label_at_bound_is_an_error(m):
+    dims = (20, 10, 10)
+    lab = torch.zeros(2000, dtype=torch.int32, device="cuda")
+    lab[1234] = 50
+    with pytest.raises(m.MSCError) as e:
+        m.adjacency_grid(lab, dims, 14, label_bound=50)
+    assert e.value.code == m.ERR_ARG
+    a, b = m.adjacency_grid(lab, dims, 14, label_bound=51)
+    assert a.tolist() == [0] and b.tolist() == [50]
+
+
+def torch_pairs(lab, dims, conn, shift):
+    """Plain PyTorch: every edge's (lo << shift) | hi, de-duplicated and sorted."""
+    nx, ny, nz = dims
+    L = lab.reshape(nz, ny, nx).long()
+    keys = []
+    for dx, dy, dz in POS[: 3 if conn == 6 else 7]:
+        A = L[: nz - dz, : ny - dy, : nx - dx]
+        B = L[dz:, dy:, dx:]
+        on = (A >= 0) & (B >= 0) & (A != B)
+        lo = torch.minimum(A, B)[on]
+        hi = torch.maximum(A, B)[on]
+        keys.append((lo << shift) | hi)
+        del A, B, on, lo, hi
+    return torch.unique(torch.cat(keys))
+
+
+@pytest.mark.parametrize("kind", ["smooth", "noise"])
+def test_full_size_512(m, kind):
+    """512^3 segmentations (the benchmarked size): the cell adjacency and the
+    maximum adjacency equal the set of pairs over every edge."""
+    E = 512
+    dims = (E, E, E)
+    f = (workloads.field_smooth(edge=E, seed=1, device="cuda") if kind == "smooth"
+         else workloads.field_noise(edge=E, seed=1, device="cuda")).reshape(-1)
+    order, asc, desc, ms, cells = m.segment(f, dims)
+    del order, asc, f
+    torch.cuda.empty_cache()
+    n = E ** 3
+    for lab, bound in ((desc, n), (ms, cells)):
+        shift = max(int(bound - 1).bit_length(), 0)
+        a, b = m.adjacency_grid(lab, dims, 14, label_bound=bound)
+        want = torch_pairs(lab, dims, 14, shift)
+        assert a.numel() == want.numel()
+        got = (a.long() << shift) | b.long()
+        assert torch.equal(got, want)
+        del a, b, want, got
+        torch.cuda.empty_cache()

@@ -29,7 +29,8 @@ def declared_symbols():
 def test_header_declares_the_boundary():
     syms = declared_symbols()
     for name in ["msc_order", "msc_steepest_grid", "msc_steepest_csr", "msc_compress", "msc_ms_id",
-                 "msc_segment", "msc_cc_mask", "msc_cc_mesh", "msc_workspace_bytes", "msc_status_string"]:
+                 "msc_segment", "msc_cc_mask", "msc_cc_mesh", "msc_adjacency_grid", "msc_workspace_bytes",
+                 "msc_status_string"]:
         assert name in syms
 
 
@@ -72,6 +73,18 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert m.msc_server_create(0, 1, 0) == 0
     assert m.msc_server_create(1 << 20, 0, 0) == 0
     assert m.msc_server_submit(0, m.Job())[0] == m.ERR_ARG
+    # region adjacency: connectivity, label bound, capacity, workspace size and alignment
+    ws = m.msc_workspace_bytes(m.OP_ADJACENCY, 64)
+    assert ws > 7 * 64 * 8 * 2
+    assert m.msc_workspace_bytes(m.OP_ADJACENCY, (2 ** 31) // 7 + 1) == 0
+    args = dict(a=16, b=16, cap=4, num_pairs=16, ws=256, ws_bytes=ws, status=16, stream=0)
+    assert m.msc_adjacency_grid(16, (4, 4, 4), 8, 64, **args) == m.ERR_ARG
+    assert m.msc_adjacency_grid(16, (4, 4, 4), 14, 0, **args) == m.ERR_ARG
+    assert m.msc_adjacency_grid(16, (4, 4, 4), 14, 64, **dict(args, cap=-1)) == m.ERR_ARG
+    assert m.msc_adjacency_grid(16, (4, 4, 4), 14, 64, **dict(args, a=0)) == m.ERR_ARG
+    assert m.msc_adjacency_grid(16, (4, 4, 4), 14, 64, **dict(args, ws=256 + 8)) == m.ERR_ARG
+    assert m.msc_adjacency_grid(16, (4, 4, 4), 14, 64, **dict(args, ws_bytes=ws - 1)) == m.ERR_WS
+    assert m.msc_adjacency_grid(16, (1024, 1024, 1024), 6, 64, **args) == m.ERR_TOO_LARGE
 
 
 def test_no_cpu_fallback():
