@@ -48,6 +48,7 @@ def parse_args():
     ap.add_argument("--no-serve", action="store_true", help="skip the served-request rate sweep")
     ap.add_argument("--serve-requests", type=int, default=64, help="requests per arrival rate")
     ap.add_argument("--no-density", action="store_true", help="skip the 1024^3 mask-density sweep")
+    ap.add_argument("--no-adjacency", action="store_true", help="skip the region-adjacency measurement")
     return ap.parse_args()
 
 
@@ -419,6 +420,10 @@ def run_ours(args):
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         out["cpu_baseline"] = cpu_baseline(f_smooth, f_noise, mask, E)
+    if not args.no_adjacency:
+        out["adjacency"] = adjacency_bench(dev, dims, [
+            ("smooth", "desc", seg_out[0][2], n), ("smooth", "ms", seg_out[0][3], int(cells[0].item())),
+            ("noise", "desc", seg_out[1][2], n), ("noise", "ms", seg_out[1][3], int(cells[1].item()))])
     if not args.no_batch:
         del f_smooth, f_noise, mask, row, col, seg_out, lab, mlab, ws
         torch.cuda.empty_cache()
@@ -599,6 +604,65 @@ def serve_bench(dev, count):
         "latency": "host submit to completion seen by the server (completion callback)",
         "rates": rates, "input_gen_s": round(gen_s, 1), "clocks": clk.summary(),
     }
+
+
+# ---------------------------------------------------------------------------
+# region adjacency (the Morse-Smale connectivity preview) of the step's own
+# segmentation outputs: pairs of maxima whose manifolds touch and pairs of
+# cells that share a boundary, 14-neighbour triangulation
+
+
+def adjacency_bench(dev, dims, cases, reps=3):
+    import torch
+
+    import paper_2409_03771_gb300 as msc
+
+    n = dims[0] * dims[1] * dims[2]
+    ws = torch.empty(msc.msc_workspace_bytes(msc.OP_ADJACENCY, n), dtype=torch.uint8, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    k = torch.zeros(1, dtype=torch.int64, device=dev)
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    peak, peak_kind = measured_peaks()
+    rows = []
+    for field, labels, lab, bound in cases:
+        cap = 7 * n  # room for every pair: nothing is cut
+        a = torch.empty(cap, dtype=torch.int32, device=dev)
+        b = torch.empty(cap, dtype=torch.int32, device=dev)
+
+        def run():
+            r = msc.msc_adjacency_grid(lab, dims, 14, bound, a, b, cap, k, ws, ws.numel(), st, stream)
+            assert r == 0, msc.msc_status_string(r)
+
+        run()
+        torch.cuda.synchronize()
+        msc.msc_trace_reset()
+        msc.msc_trace_enable(True)
+        ev0.record(stream)
+        for _ in range(reps):
+            run()
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        msc.msc_trace_enable(False)
+        trace = msc.msc_trace_collect()
+        if int(st.item()) != 0:
+            raise RuntimeError(f"adjacency of {field} {labels}: device status {int(st.item())}")
+        ms = ev0.elapsed_time(ev1) / reps
+        cnt, tot = trace.get("adjacency.emit", (1, 0.0))
+        emit_ms = tot / max(cnt, 1)
+        # the emit kernel's algorithmic traffic: every label read once (the
+        # tile de-duplicated keys it writes are data-dependent and excluded)
+        emit_gbs = 4 * n / (emit_ms / 1e3) / 1e9 if emit_ms > 0 else None
+        rows.append({
+            "field": field, "labels": labels, "label_bound": bound, "pairs": int(k.item()), "ms": round(ms, 3),
+            "vertices_per_s": n / (ms / 1e3),
+            "kernels_ms": {lbl: round(t / c, 4) for lbl, (c, t) in sorted(trace.items(), key=lambda kv: -kv[1][1])},
+            "emit_roofline": {"bound": "hbm", "achieved": None if emit_gbs is None else round(emit_gbs, 1),
+                              "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
+                              "frac": None if emit_gbs is None else round(emit_gbs / peak, 4)}})
+        del a, b
+    return {"workload": f"adjacency of the step's {dims[0]}^3 maximum labels and cell ids, 14-neighbour link",
+            "rows": rows}
 
 
 # ---------------------------------------------------------------------------

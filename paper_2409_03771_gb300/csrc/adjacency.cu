@@ -6,13 +6,13 @@
 // complex that the paper's related work builds from the segmentations, and
 // the edges of an extremum graph (Conclusion).
 //
-// 1. k_adj_emit: one CTA per 32 x 8 x 4 tile stages the tile's labels and
-//    its +1 halo in shared memory, follows every positive link offset of
-//    every vertex (each edge once), and de-duplicates the pair keys
-//    (lo << shift) | hi in a shared hash set: a region boundary crosses a
-//    tile in many edges but few pairs.  The distinct keys of the tile are
-//    appended to a global buffer with one atomic per tile; a key that finds
-//    no free slot within a few probes is appended on its own.
+// 1. k_adj_emit: warps march rows of 32 vertices through z with two planes
+//    of labels in registers, follow every positive link offset of every
+//    vertex (each edge once), and de-duplicate the pair keys
+//    (lo << shift) | hi in a hash set per CTA in shared memory: a region
+//    boundary crosses a tile in many edges but few pairs.  The set's keys
+//    are appended to a global buffer with one atomic per flush; a key that
+//    finds no free slot within a few probes is appended on its own.
 // 2. The appended keys are radix-sorted (keys only).
 // 3. k_adj_heads / k_adj_scan / k_adj_write keep the first key of every run
 //    of equal keys and split it into (a, b).
@@ -26,32 +26,25 @@ namespace msc {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kTX = 32, kTY = 8, kTZ = 4;  // warp w owns row y = w of each z plane
-constexpr int kHX = kTX + 1, kHY = kTY + 1, kHZ = kTZ + 1;  // with the +1 halo
-constexpr int kSetSlots = 4096;  // shared hash set: 32 KiB of keys
-constexpr int kProbes = 32;
+constexpr int kTX = 32, kTY = 8;  // a tile: 32 x 8 rows, warp w owns row y0 + w
+constexpr int kZR = 32;           // planes a tile marches through
+constexpr int kAhead = 2;         // planes loaded ahead of their use
+constexpr int kCheckDense = 2;    // planes between checks of the set's fill where boundaries are dense
+constexpr int kCheckSparse = 8;   // ... and where the set stayed nearly empty
+constexpr int kSetBits = 12;
+constexpr int kSetSlots = 1 << kSetBits;  // shared hash set: 32 KiB of keys
+constexpr int kProbes = 16;
 constexpr unsigned long long kNoKey = ~0ull;
 constexpr int kChunk = 4096;  // sorted keys per block in the unique pass
 constexpr int kPer = kChunk / kThreads;
 
-// positive link offsets: the three face directions, then the four
-// diagonals of the Freudenthal split (x, y, z)
-__constant__ int8_t c_off[7][3] = {{1, 0, 0}, {0, 1, 0}, {0, 0, 1}, {1, 1, 0}, {1, 0, 1}, {0, 1, 1}, {1, 1, 1}};
-
-__device__ __forceinline__ unsigned long long mix64(unsigned long long k) {
-    // 64-bit finaliser of MurmurHash3
-    k ^= k >> 33;
-    k *= 0xff51afd7ed558ccdull;
-    k ^= k >> 33;
-    k *= 0xc4ceb9fe1a85ec53ull;
-    k ^= k >> 33;
-    return k;
-}
+// Positive link offsets k = 0..6: the three face directions (1,0,0),
+// (0,1,0), (0,0,1), then the four diagonals of the Freudenthal split
+// (1,1,0), (1,0,1), (0,1,1), (1,1,1); conn 6 follows the first three.
 
 struct EmitArgs {
     const int32_t* label;
     int32_t nx, ny, nz;
-    int half;     // positive offsets followed: 3 (conn 6) or 7 (conn 14)
     int32_t bound;
     int shift;
     unsigned long long* out;
@@ -68,92 +61,229 @@ __device__ __forceinline__ void append_global(const EmitArgs& a, unsigned long l
         record_error(a.status, MSC_ERR_INTERNAL);  // more keys than edges: impossible
 }
 
+// Key of the pair of labels c and m, or kNoKey when m < 0.
+__device__ __forceinline__ unsigned long long pair_key(const EmitArgs& a, int32_t c, int32_t m) {
+    if (m < 0) return kNoKey;
+    const uint32_t lo = (uint32_t)min(c, m), hi = (uint32_t)max(c, m);
+    return ((unsigned long long)lo << a.shift) | hi;
+}
+
+// Home slot of a key in the shared set: a multiplicative hash of both
+// halves (the set is rebuilt per tile, so a cheap hash suffices).
+__device__ __forceinline__ uint32_t set_home(unsigned long long key) {
+    const uint32_t h = (uint32_t)key * 0x9E3779B1u ^ (uint32_t)(key >> 32) * 0x85EBCA77u;
+    return h >> (32 - kSetBits);
+}
+
+// Inserts `key` (kNoKey = nothing) into the tile's shared set.  Called by
+// the whole warp; records new slots in s_used with one shared atomic per
+// warp.
+__device__ __forceinline__ void set_insert(const EmitArgs& a, unsigned long long key, unsigned long long* s_set,
+                                           uint16_t* s_used, uint32_t* s_nused, int lane) {
+    // a boundary usually crosses neighbouring lanes with the same pair
+    const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
+    int new_slot = -1;
+    if (key != kNoKey && !(lane > 0 && prev == key)) {
+        uint32_t h = set_home(key);
+        bool placed = false;
+        for (int p = 0; p < kProbes; ++p) {
+            const unsigned long long cur = s_set[h];
+            if (cur == key) {
+                placed = true;
+                break;
+            }
+            if (cur == kNoKey) {
+                const unsigned long long old = atomicCAS(&s_set[h], kNoKey, key);
+                if (old == kNoKey) new_slot = (int)h;
+                if (old == kNoKey || old == key) {
+                    placed = true;
+                    break;
+                }
+            }
+            h = (h + 1) & (kSetSlots - 1);
+        }
+        if (!placed) append_global(a, key);
+    }
+    const uint32_t fresh = __ballot_sync(0xffffffffu, new_slot >= 0);
+    if (fresh) {
+        const int leader = __ffs(fresh) - 1;
+        uint32_t base = 0;
+        if (lane == leader) base = atomicAdd(s_nused, (uint32_t)__popc(fresh));
+        base = __shfl_sync(0xffffffffu, base, leader);
+        if (new_slot >= 0) s_used[base + __popc(fresh & lanemask_lt())] = (uint16_t)new_slot;
+    }
+}
+
+// Labels of plane z of rows y and y + 1 of a tile (lanes hold x0 + lane)
+// and the labels at x0 + 32 of both rows (every lane the same); -1 outside
+// the grid.
+struct Plane {
+    int32_t c, u;  // (x, y, z), (x, y + 1, z)
+    int32_t e, f;  // (x0 + 32, y, z), (x0 + 32, y + 1, z)
+};
+
+// Plane z of the two rows; -1 past the grid.  Only the row's own label (c)
+// is checked against the bound: every vertex is the own label of exactly
+// one (warp, lane, plane), so each label is checked once; an unchecked
+// label past the bound can only make a key of a call that reports
+// MSC_ERR_ARG.
+__device__ __forceinline__ Plane load_plane(const EmitArgs& a, int x, int y, int xe, int z) {
+    Plane p;
+    const bool in_z = z < a.nz;
+    const int32_t* r = a.label + (int64_t)a.nx * y + (int64_t)a.nx * a.ny * z;
+    p.c = in_z && y < a.ny && x < a.nx ? __ldg(r + x) : -1;
+    p.u = in_z && y + 1 < a.ny && x < a.nx ? __ldg(r + a.nx + x) : -1;
+    p.e = in_z && y < a.ny && xe < a.nx ? __ldg(r + xe) : -1;
+    p.f = in_z && y + 1 < a.ny && xe < a.nx ? __ldg(r + a.nx + xe) : -1;
+    return p;
+}
+
+__device__ __forceinline__ int32_t checked(const EmitArgs& a, int32_t l) {
+    if (l >= a.bound) {
+        record_error(a.status, MSC_ERR_ARG);
+        return -1;
+    }
+    return l;
+}
+
+// Called by the whole CTA: when `force` or the set holds a quarter of its
+// slots, appends the set's keys to the global buffer (one atomic) and
+// empties the set.  Returns the planes to the next check (the same in every
+// thread): few when the set is filling, more when it stayed nearly empty.
+__device__ __forceinline__ int flush_set(const EmitArgs& a, unsigned long long* s_set, const uint16_t* s_used,
+                                      uint32_t* s_nused, uint32_t* s_base, bool force) {
+    const int tid = threadIdx.x;
+    const bool go = __syncthreads_or(force || (tid == 0 && *s_nused >= kSetSlots / 4));
+    const uint32_t nu = *s_nused;  // every insert is behind the barrier above
+    const int next = nu < kSetSlots / 16 ? kCheckSparse : kCheckDense;
+    if (!go) {
+        __syncthreads();  // nobody may insert before every thread has read s_nused
+        return next;
+    }
+    __syncthreads();
+    if (tid == 0) {
+        *s_base = nu ? atomicAdd(reinterpret_cast<uint32_t*>(a.count), nu) : 0u;
+        *s_nused = 0;
+    }
+    __syncthreads();
+    for (uint32_t i = tid; i < nu; i += kThreads) {
+        const uint32_t slot = s_used[i];
+        const uint32_t pos = *s_base + i;
+        if ((int64_t)pos < a.cap)
+            a.out[pos] = s_set[slot];
+        else
+            record_error(a.status, MSC_ERR_INTERNAL);
+        s_set[slot] = kNoKey;  // cleared for the keys that follow
+    }
+    __syncthreads();
+    return next;
+}
+
+// HALF: positive offsets followed, 3 (conn 6) or 7 (conn 14).  A CTA takes
+// tiles of 32 x 8 rows by kZR planes; each warp marches its row through the
+// planes with the labels of planes z and z + 1 in registers (neighbours in
+// x from a lane shuffle, in y from the row above, which L2 serves to both
+// warps that read it), so every label comes from DRAM about once and the
+// only barriers are the set's fill checks.
+template <int HALF>
 __global__ void __launch_bounds__(kThreads) k_adj_emit(const EmitArgs a) {
     __shared__ unsigned long long s_set[kSetSlots];
     __shared__ uint16_t s_used[kSetSlots];
-    __shared__ int32_t s_lab[kHZ][kHY][kHX];
     __shared__ uint32_t s_nused, s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     for (int i = tid; i < kSetSlots; i += kThreads) s_set[i] = kNoKey;
     if (tid == 0) s_nused = 0;
-    const int64_t tx = (a.nx + kTX - 1) / kTX, ty = (a.ny + kTY - 1) / kTY, tz = (a.nz + kTZ - 1) / kTZ;
-    const int64_t ntiles = tx * ty * tz;
-    const int64_t plane = (int64_t)a.nx * a.ny;
-    for (int64_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
-        const int64_t bx = t % tx, by = (t / tx) % ty, bz = t / (tx * ty);
-        const int x0 = (int)(bx * kTX), y0 = (int)(by * kTY), z0 = (int)(bz * kTZ);
-        // stage labels (tile + halo; -1 outside the grid); a label at or
-        // above the bound is an argument error and counts as unlabelled
-        for (int i = tid; i < kHX * kHY * kHZ; i += kThreads) {
-            const int hx = i % kHX, hy = (i / kHX) % kHY, hz = i / (kHX * kHY);
-            const int x = x0 + hx, y = y0 + hy, z = z0 + hz;
-            int32_t l = -1;
-            if (x < a.nx && y < a.ny && z < a.nz) {
-                l = __ldg(a.label + x + (int64_t)a.nx * y + plane * z);
-                if (l >= a.bound) {
-                    record_error(a.status, MSC_ERR_ARG);
-                    l = -1;
+    __syncthreads();
+    // tile counts fit 32 bits: n < 2^31 vertices and every tile holds one
+    const uint32_t tx = (a.nx + kTX - 1) / kTX, ty = (a.ny + kTY - 1) / kTY, tz = (a.nz + kZR - 1) / kZR;
+    const uint32_t ntiles = tx * ty * tz;
+    for (uint32_t t = blockIdx.x; t < ntiles; t += gridDim.x) {
+        const uint32_t txy = tx * ty, bz = t / txy, rem = t - bz * txy, by = rem / tx, bx = rem - by * tx;
+        const int x0 = (int)bx * kTX, x = x0 + lane, xe = x0 + kTX, y = (int)by * kTY + warp;
+        const int zs = (int)bz * kZR, ze = min(zs + kZR, a.nz);
+        Plane cur = load_plane(a, x, y, xe, zs);
+        Plane q[kAhead];  // planes z + 1 .. z + kAhead, loads in flight
+#pragma unroll
+        for (int i = 0; i < kAhead; ++i) q[i] = load_plane(a, x, y, xe, zs + 1 + i);
+        cur.c = checked(a, cur.c);
+        // (x + 1) neighbours of the current plane: the next lane's label,
+        // or the label at x0 + 32 for the last lane
+        int32_t xn = __shfl_down_sync(0xffffffffu, cur.c, 1), dn = __shfl_down_sync(0xffffffffu, cur.u, 1);
+        if (lane == 31) {
+            xn = cur.e;
+            dn = cur.f;
+        }
+        int until = kCheckDense;  // planes to the next check of the set (uniform across the CTA)
+#pragma unroll 1
+        for (int z = zs; z < ze; ++z) {
+            const Plane nx1 = {checked(a, q[0].c), q[0].u, q[0].e, q[0].f};
+#pragma unroll
+            for (int i = 0; i + 1 < kAhead; ++i) q[i] = q[i + 1];
+            q[kAhead - 1] = load_plane(a, x, y, xe, z + 1 + kAhead);  // used kAhead planes from now
+            int32_t xn1 = __shfl_down_sync(0xffffffffu, nx1.c, 1), dn1 = __shfl_down_sync(0xffffffffu, nx1.u, 1);
+            if (lane == 31) {
+                xn1 = nx1.e;
+                dn1 = nx1.f;
+            }
+            const int32_t c0 = cur.c;
+            // neighbours in the order of the offsets k = 0..6
+            const int32_t nb[7] = {xn, cur.u, nx1.c, dn, xn1, nx1.u, dn1};
+            uint32_t diff = 0;  // nonzero iff some neighbour's label differs from c0
+#pragma unroll
+            for (int k = 0; k < HALF; ++k) diff |= (uint32_t)(nb[k] ^ c0);
+            // usually no lane of the row sits at a region boundary
+            if (__any_sync(0xffffffffu, diff != 0 && c0 >= 0)) {
+                // the distinct labels across this vertex's boundary edges:
+                // one for a boundary between two regions, two where three
+                // meet; offsets with a third or later one go to `extra`
+                int32_t m0 = -1, m1 = -1;
+                uint32_t extra = 0;
+                if (c0 >= 0) {
+#pragma unroll
+                    for (int k = 0; k < HALF; ++k) {
+                        const int32_t m = nb[k];
+                        if (m >= 0 && m != c0 && m != m0 && m != m1) {
+                            if (m0 < 0)
+                                m0 = m;
+                            else if (m1 < 0)
+                                m1 = m;
+                            else
+                                extra |= 1u << k;
+                        }
+                    }
+                }
+                // rounds: m0, m1 when some lane has one, then one round per
+                // offset in the warp's union of `extra`
+                uint32_t wextra = __reduce_or_sync(0xffffffffu, extra);
+                const bool two = __any_sync(0xffffffffu, m1 >= 0);
+                for (int round = 0;; ++round) {
+                    int32_t m;
+                    if (round == 0) {
+                        m = m0;
+                    } else if (round == 1 && two) {
+                        m = m1;
+                    } else {
+                        if (!wextra) break;
+                        const int k = __ffs(wextra) - 1;
+                        wextra &= wextra - 1;
+                        m = extra >> k & 1u ? (k == 0 ? nb[0] : k == 1 ? nb[1] : k == 2 ? nb[2] : k == 3 ? nb[3]
+                                               : k == 4 ? nb[4] : k == 5 ? nb[5] : nb[6])
+                                            : -1;
+                    }
+                    set_insert(a, pair_key(a, c0, m), s_set, s_used, &s_nused, lane);
                 }
             }
-            s_lab[hz][hy][hx] = l;
+            cur = nx1;
+            xn = xn1;
+            dn = dn1;
+            // hand the set's keys to the global buffer when it is a quarter
+            // full, checked often enough that the keys added before the next
+            // check still find room (a full set only costs de-duplication:
+            // keys that find no slot go out on their own), and at the
+            // tile's end
+            const bool last = z + 1 == ze;
+            if (--until == 0 || last) until = flush_set(a, s_set, s_used, &s_nused, &s_base, last);
         }
-        __syncthreads();
-        for (int z = 0; z < kTZ; ++z) {
-            // halo vertices (x = 32, y = 8 or z = 4 in the tile) are only
-            // ever edge ends: s_lab holds -1 past the grid
-            const int32_t l = s_lab[z][warp][lane];
-            for (int k = 0; k < a.half; ++k) {
-                const int32_t m = s_lab[z + c_off[k][2]][warp + c_off[k][1]][lane + c_off[k][0]];
-                unsigned long long key = kNoKey;
-                if (l >= 0 && m >= 0 && l != m) {
-                    const uint32_t lo = (uint32_t)min(l, m), hi = (uint32_t)max(l, m);
-                    key = ((unsigned long long)lo << a.shift) | hi;
-                }
-                // a boundary usually crosses neighbouring lanes with the same pair
-                const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
-                if (key == kNoKey || (lane > 0 && prev == key)) continue;
-                uint32_t h = (uint32_t)mix64(key) & (kSetSlots - 1);
-                bool placed = false;
-                for (int p = 0; p < kProbes; ++p) {
-                    const unsigned long long cur = s_set[h];
-                    if (cur == key) {
-                        placed = true;
-                        break;
-                    }
-                    if (cur == kNoKey) {
-                        const unsigned long long old = atomicCAS(&s_set[h], kNoKey, key);
-                        if (old == kNoKey) {
-                            s_used[atomicAdd(&s_nused, 1u)] = (uint16_t)h;
-                            placed = true;
-                            break;
-                        }
-                        if (old == key) {
-                            placed = true;
-                            break;
-                        }
-                    }
-                    h = (h + 1) & (kSetSlots - 1);
-                }
-                if (!placed) append_global(a, key);
-            }
-        }
-        __syncthreads();
-        const uint32_t nu = s_nused;
-        if (tid == 0 && nu) s_base = atomicAdd(reinterpret_cast<uint32_t*>(a.count), nu);
-        __syncthreads();
-        for (uint32_t i = tid; i < nu; i += kThreads) {
-            const uint32_t slot = s_used[i];
-            const uint32_t pos = s_base + i;
-            if ((int64_t)pos < a.cap)
-                a.out[pos] = s_set[slot];
-            else
-                record_error(a.status, MSC_ERR_INTERNAL);
-            s_set[slot] = kNoKey;  // cleared for the next tile
-        }
-        __syncthreads();
-        if (tid == 0) s_nused = 0;
-        // the next tile's staging loop writes s_lab only after this barrier
-        // and s_nused is read after the staging barrier
     }
 }
 
@@ -227,7 +357,9 @@ __global__ void __launch_bounds__(1024) k_adj_scan(uint32_t* chunk_heads, const 
 }
 
 // Writes the heads of each chunk at their ranks: a = key >> shift,
-// b = key & (2^shift - 1); ranks at or beyond `out_cap` are dropped.
+// b = key & (2^shift - 1); ranks at or beyond `out_cap` are dropped.  The
+// chunk goes in kPer rounds of one key per thread (coalesced); a round's
+// ranks come from a block-wide count of the heads before each thread.
 __global__ void __launch_bounds__(kThreads) k_adj_write(const unsigned long long* __restrict__ keys,
                                                         const int32_t* d_count, int64_t cap,
                                                         const uint32_t* __restrict__ chunk_base, int shift,
@@ -238,35 +370,32 @@ __global__ void __launch_bounds__(kThreads) k_adj_write(const unsigned long long
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long mask = (1ull << shift) - 1;
     for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x) {
-        // thread tid takes the kPer consecutive keys [c*kChunk + tid*kPer, ...)
-        const int64_t i0 = c * kChunk + (int64_t)tid * kPer;
-        uint32_t heads = 0;  // bit j: key i0 + j starts a run
+        int64_t run = chunk_base[c];
         for (int j = 0; j < kPer; ++j) {
-            const int64_t i = i0 + j;
-            if (i < m && (i == 0 || keys[i] != keys[i - 1])) heads |= 1u << j;
-        }
-        const uint32_t cnt = __popc(heads);
-        uint32_t incl = cnt;
-        for (int o = 1; o < 32; o <<= 1) {
-            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
-            if (lane >= o) incl += t;
-        }
-        if (lane == 31) s_w[warp] = incl;
-        __syncthreads();
-        uint32_t before = 0;
-        for (int w = 0; w < warp; ++w) before += s_w[w];
-        int64_t r = (int64_t)chunk_base[c] + before + incl - cnt;
-        for (int j = 0; j < kPer; ++j) {
-            if (heads >> j & 1u) {
-                if (r < out_cap) {
-                    const unsigned long long k = keys[i0 + j];
-                    out_a[r] = (int32_t)(k >> shift);
-                    out_b[r] = (int32_t)(k & mask);
-                }
-                ++r;
+            const int64_t i = c * kChunk + (int64_t)j * kThreads + tid;
+            unsigned long long k = 0;
+            bool head = false;
+            if (i < m) {
+                k = keys[i];
+                head = i == 0 || k != keys[i - 1];
             }
+            const uint32_t bal = __ballot_sync(0xffffffffu, head);
+            if (lane == 0) s_w[warp] = __popc(bal);
+            __syncthreads();
+            uint32_t before = __popc(bal & lanemask_lt()), total = 0;
+            for (int w = 0; w < kThreads / 32; ++w) {
+                const uint32_t c_w = s_w[w];
+                before += w < warp ? c_w : 0u;
+                total += c_w;
+            }
+            const int64_t r = run + before;
+            if (head && r < out_cap) {
+                out_a[r] = (int32_t)(k >> shift);
+                out_b[r] = (int32_t)(k & mask);
+            }
+            run += total;
+            __syncthreads();  // s_w is rewritten by the next round
         }
-        __syncthreads();
     }
 }
 
@@ -303,11 +432,15 @@ int run_adjacency_grid(const int32_t* label, msc_grid g, int conn, int32_t bound
     if (!c.ok()) return MSC_ERR_WS;
     MSC_TRY(cudaMemsetAsync(ctl, 0, 64 * sizeof(int32_t), s));
     const int shift = ceil_log2(bound);
-    EmitArgs ea{label, g.nx, g.ny, g.nz, conn == 6 ? 3 : 7, bound, shift, k0, ctl, cap, status};
-    const int64_t tiles = ceil_div(g.nx, kTX) * ceil_div(g.ny, kTY) * ceil_div(g.nz, kTZ);
+    EmitArgs ea{label, g.nx, g.ny, g.nz, bound, shift, k0, ctl, cap, status};
+    const int64_t tiles = ceil_div(g.nx, kTX) * ceil_div(g.ny, kTY) * ceil_div(g.nz, kZR);
     {
         TraceScope ts_("adjacency.emit", s);
-        k_adj_emit<<<blocks_for(tiles, 4), kThreads, 0, s>>>(ea);
+        // persistent: as many CTAs as fit on the GPU at once
+        auto kern = conn == 6 ? k_adj_emit<3> : k_adj_emit<7>;
+        int occ = 0;
+        MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
+        kern<<<blocks_for(tiles, std::max(occ, 1)), kThreads, 0, s>>>(ea);
     }
     MSC_LAUNCHED();
     bool in_alt = false;
