@@ -69,6 +69,7 @@ def _load():
             "oracle_cc_csr": (i32, [P, P, i32, P]),
             "oracle_cc_grid_at": (i32, [P, i32, i32, i32, i32, i64, P, P]),
             "oracle_adjacency_grid": (i32, [P, i32, i32, i32, i32, P, P, i64, P]),
+            "oracle_extremum_graph": (i32, [P, P, i32, i32, i32, i32, i32, P, P, P, i64, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -233,3 +234,22 @@ def adjacency_grid(label, dims, conn: int = 14):
     _check(_load().oracle_adjacency_grid(_ptr(lab), nx, ny, nz, conn, _ptr(a), _ptr(b), cnt.value,
                                          ctypes.byref(cnt)), "adjacency_grid")
     return a[:cnt.value], b[:cnt.value]
+
+
+def extremum_graph(label, order, dims, conn: int = 14, sense: int = 1):
+    """Arcs (a, b, saddle) of the extremum graph: pairs of different
+    non-negative labels (maximum labels for sense +1, minimum labels for -1)
+    that meet across an edge, in lexicographic order, each with the end
+    vertex of its highest (maxima) or lowest (minima) crossing edge in the
+    order: three int32 arrays."""
+    nx, ny, nz = dims
+    lab = _c(label, np.int32).ravel()
+    o = _c(order, np.int32).ravel()
+    cnt = ctypes.c_int64()
+    _check(_load().oracle_extremum_graph(_ptr(lab), _ptr(o), nx, ny, nz, conn, sense, 0, 0, 0, 0,
+                                         ctypes.byref(cnt)), "extremum_graph")
+    k = cnt.value
+    a, b, s = (np.empty(max(k, 1), np.int32) for _ in range(3))
+    _check(_load().oracle_extremum_graph(_ptr(lab), _ptr(o), nx, ny, nz, conn, sense, _ptr(a), _ptr(b), _ptr(s), k,
+                                         ctypes.byref(cnt)), "extremum_graph")
+    return a[:k], b[:k], s[:k]

@@ -549,3 +549,87 @@ int oracle_adjacency_grid(const int32_t* label, int32_t nx, int32_t ny, int32_t 
     *count = k;
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* Arcs of the extremum graph with their saddles (Conclusion: the extremum
+ * graph that the segmentations make computable).  `label` holds maximum
+ * labels (sense = +1) or minimum labels (sense = -1) and `order` the vertex
+ * order.  Every edge (u, v) between two different non-negative labels a, b
+ * crosses from one region into the other at a level: for maxima the lower
+ * of its two ends in the order (a path between the two maxima through this
+ * edge must come down to it), for minima the higher.  The saddle of the
+ * pair (min(a,b), max(a,b)) is the end vertex with the highest such level
+ * over all of the pair's edges for maxima, the lowest for minima.  Output:
+ * the distinct pairs in lexicographic order with their saddle vertex; cap
+ * and *count as for oracle_adjacency_grid.                                  */
+
+typedef struct {
+    uint64_t key;  /* lo << 32 | hi */
+    int32_t level; /* order of the crossing vertex */
+    int32_t vertex;
+} or_arc;
+
+static int or_cmp_arc(const void* x, const void* y) {
+    const or_arc* p = (const or_arc*)x;
+    const or_arc* q = (const or_arc*)y;
+    if (p->key != q->key) return p->key < q->key ? -1 : 1;
+    return (p->level > q->level) - (p->level < q->level);
+}
+
+int oracle_extremum_graph(const int32_t* label, const int32_t* order, int32_t nx, int32_t ny, int32_t nz,
+                          int conn, int sense, int32_t* a_out, int32_t* b_out, int32_t* saddle_out,
+                          int64_t cap, int64_t* count) {
+    if (!or_grid_ok(nx, ny, nz) || !label || !order || !count || (conn != 6 && conn != 14) ||
+        (sense != 1 && sense != -1) || cap < 0)
+        return OR_ERR_ARG;
+    const int (*off)[3] = conn == 6 ? OR_FACE6 : OR_FREUD;
+    const int64_t n = (int64_t)nx * ny * nz;
+    int64_t m = 0, mcap = 1024;
+    or_arc* arcs = (or_arc*)malloc((size_t)mcap * sizeof(or_arc));
+    if (!arcs) return OR_ERR_OOM;
+    for (int64_t v = 0; v < n; ++v) {
+        const int64_t x = v % nx, y = (v / nx) % ny, z = v / ((int64_t)nx * ny);
+        for (int k = 0; k < conn; k += 2) { /* each edge once */
+            const int64_t xx = x + off[k][0], yy = y + off[k][1], zz = z + off[k][2];
+            if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz) continue;
+            const int64_t u = xx + (int64_t)nx * (yy + (int64_t)ny * zz);
+            const int32_t la = label[v], lb = label[u];
+            if (la < 0 || lb < 0 || la == lb) continue;
+            if (m == mcap) {
+                mcap *= 2;
+                or_arc* p2 = (or_arc*)realloc(arcs, (size_t)mcap * sizeof(or_arc));
+                if (!p2) {
+                    free(arcs);
+                    return OR_ERR_OOM;
+                }
+                arcs = p2;
+            }
+            const int lower_is_v = order[v] < order[u];
+            /* maxima: the crossing vertex is the lower end; minima: the higher */
+            const int64_t w = (sense > 0) == lower_is_v ? v : u;
+            const uint32_t lo = (uint32_t)(la < lb ? la : lb), hi = (uint32_t)(la < lb ? lb : la);
+            arcs[m].key = ((uint64_t)lo << 32) | hi;
+            arcs[m].level = order[w];
+            arcs[m].vertex = (int32_t)w;
+            ++m;
+        }
+    }
+    qsort(arcs, (size_t)m, sizeof(or_arc), or_cmp_arc);
+    int64_t k = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        if (i > 0 && arcs[i].key == arcs[i - 1].key) continue;
+        /* the run of this key is sorted by level: its last entry is the
+         * highest crossing, its first the lowest */
+        int64_t j = i;
+        while (j + 1 < m && arcs[j + 1].key == arcs[i].key) ++j;
+        if (k < cap) {
+            a_out[k] = (int32_t)(arcs[i].key >> 32);
+            b_out[k] = (int32_t)(uint32_t)arcs[i].key;
+            saddle_out[k] = sense > 0 ? arcs[j].vertex : arcs[i].vertex;
+        }
+        ++k;
+    }
+    free(arcs);
+    *count = k;
+    return OR_OK;
+}
