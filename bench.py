@@ -422,8 +422,11 @@ def run_ours(args):
         out["cpu_baseline"] = cpu_baseline(f_smooth, f_noise, mask, E)
     if not args.no_adjacency:
         out["adjacency"] = adjacency_bench(dev, dims, [
-            ("smooth", "desc", seg_out[0][2], n), ("smooth", "ms", seg_out[0][3], int(cells[0].item())),
-            ("noise", "desc", seg_out[1][2], n), ("noise", "ms", seg_out[1][3], int(cells[1].item()))])
+            ("smooth", "desc", seg_out[0][2], n, None, 0), ("smooth", "ms", seg_out[0][3], int(cells[0].item()), None, 0),
+            ("noise", "desc", seg_out[1][2], n, None, 0), ("noise", "ms", seg_out[1][3], int(cells[1].item()), None, 0),
+            # the extremum graph: maxima / minima arcs with their saddles
+            ("smooth", "desc", seg_out[0][2], n, seg_out[0][0], 1), ("smooth", "asc", seg_out[0][1], n, seg_out[0][0], -1),
+            ("noise", "desc", seg_out[1][2], n, seg_out[1][0], 1)])
     if not args.no_batch:
         del f_smooth, f_noise, mask, row, col, seg_out, lab, mlab, ws
         torch.cuda.empty_cache()
@@ -618,20 +621,25 @@ def adjacency_bench(dev, dims, cases, reps=3):
     import paper_2409_03771_gb300 as msc
 
     n = dims[0] * dims[1] * dims[2]
-    ws = torch.empty(msc.msc_workspace_bytes(msc.OP_ADJACENCY, n), dtype=torch.uint8, device=dev)
+    ws = torch.empty(msc.msc_workspace_bytes(msc.OP_EXTREMUM_GRAPH, n), dtype=torch.uint8, device=dev)
     st = torch.zeros(1, dtype=torch.int32, device=dev)
     k = torch.zeros(1, dtype=torch.int64, device=dev)
     stream = torch.cuda.current_stream(dev)
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     peak, peak_kind = measured_peaks()
     rows = []
-    for field, labels, lab, bound in cases:
+    for field, labels, lab, bound, order, sense in cases:
         cap = 7 * n  # room for every pair: nothing is cut
         a = torch.empty(cap, dtype=torch.int32, device=dev)
         b = torch.empty(cap, dtype=torch.int32, device=dev)
+        sad = torch.empty(cap if order is not None else 1, dtype=torch.int32, device=dev)
 
         def run():
-            r = msc.msc_adjacency_grid(lab, dims, 14, bound, a, b, cap, k, ws, ws.numel(), st, stream)
+            if order is None:
+                r = msc.msc_adjacency_grid(lab, dims, 14, bound, a, b, cap, k, ws, ws.numel(), st, stream)
+            else:
+                r = msc.msc_extremum_graph(lab, order, dims, 14, bound, sense, a, b, sad, cap, k, ws, ws.numel(), st,
+                                           stream)
             assert r == 0, msc.msc_status_string(r)
 
         run()
@@ -654,14 +662,16 @@ def adjacency_bench(dev, dims, cases, reps=3):
         # tile de-duplicated keys it writes are data-dependent and excluded)
         emit_gbs = 4 * n / (emit_ms / 1e3) / 1e9 if emit_ms > 0 else None
         rows.append({
-            "field": field, "labels": labels, "label_bound": bound, "pairs": int(k.item()), "ms": round(ms, 3),
+            "field": field, "labels": labels, "op": "adjacency" if order is None else f"extremum graph ({'+' if sense > 0 else '-'})",
+            "label_bound": bound, "pairs": int(k.item()), "ms": round(ms, 3),
             "vertices_per_s": n / (ms / 1e3),
             "kernels_ms": {lbl: round(t / c, 4) for lbl, (c, t) in sorted(trace.items(), key=lambda kv: -kv[1][1])},
             "emit_roofline": {"bound": "hbm", "achieved": None if emit_gbs is None else round(emit_gbs, 1),
                               "peak": peak, "unit": "GB/s", "peak_kind": peak_kind,
                               "frac": None if emit_gbs is None else round(emit_gbs / peak, 4)}})
-        del a, b
-    return {"workload": f"adjacency of the step's {dims[0]}^3 maximum labels and cell ids, 14-neighbour link",
+        del a, b, sad
+    return {"workload": (f"adjacency of the step's {dims[0]}^3 maximum labels and cell ids, and the extremum graph "
+                         f"(arcs + saddles) of its maximum and minimum labels; 14-neighbour link"),
             "rows": rows}
 
 

@@ -71,7 +71,8 @@ enum {
     MSC_OP_SEGMENT = 4,
     MSC_OP_CC_MASK = 5,
     MSC_OP_CC_MESH = 6,
-    MSC_OP_ADJACENCY = 7
+    MSC_OP_ADJACENCY = 7,
+    MSC_OP_EXTREMUM_GRAPH = 8
 };
 
 /* Workspace bytes needed by `op` on n vertices (nnz CSR entries for
@@ -223,6 +224,37 @@ MSC_API int msc_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32
 MSC_API int msc_adjacency_grid(const int32_t* label, msc_grid g, int32_t conn, int32_t label_bound,
                                int32_t* a, int32_t* b, int64_t cap, int64_t* num_pairs, void* ws,
                                size_t ws_bytes, int32_t* d_status, void* stream);
+
+/* Arcs of the extremum graph with their saddles (Conclusion: the
+ * segmentations make the extremum graph of a merge-tree computation
+ * available; the paper defines neither the graph nor its saddles).  The
+ * arcs are the region adjacency of msc_adjacency_grid applied to maximum
+ * labels (sense = +1) or minimum labels (sense = -1).  Every edge between
+ * two regions crosses at one of its ends: for maxima the end lower in the
+ * order (a path from one maximum to the other through the edge comes down
+ * to it), for minima the higher end.  The saddle of an arc is the crossing
+ * vertex of its highest crossing edge (maxima) or of its lowest (minima).
+ *   label      device int32[n]: desc labels (sense +1) or asc labels (-1)
+ *              as msc_segment writes them, or any labels below
+ *              label_bound (negative = unlabelled).
+ *   order      device int32[n]: the vertex order (msc_order output, a
+ *              permutation of 0..n-1; other values give unspecified
+ *              saddles).
+ *   conn, label_bound, cap: as for msc_adjacency_grid.
+ *   a, b       device int32[cap] out: the first min(cap, K) arcs, a < b,
+ *              in lexicographic order.
+ *   saddle     device int32[cap] out: the arc's saddle vertex.
+ *   num_arcs   device int64 out: K.
+ * Workspace: msc_workspace_bytes(MSC_OP_EXTREMUM_GRAPH, n, 0) (7n keys
+ * with their crossing vertices); n above (2^31 - 1) / 7 returns
+ * MSC_ERR_TOO_LARGE.
+ * Method: msc_adjacency_grid's, with each tile's shared set also keeping
+ * the highest crossing of each key, the crossing vertices sorted with the
+ * keys, and one atomic maximum per run of equal keys in a warp. */
+MSC_API int msc_extremum_graph(const int32_t* label, const int32_t* order, msc_grid g, int32_t conn,
+                               int32_t label_bound, int32_t sense, int32_t* a, int32_t* b, int32_t* saddle,
+                               int64_t cap, int64_t* num_arcs, void* ws, size_t ws_bytes, int32_t* d_status,
+                               void* stream);
 
 /* ---------------------------------------------------------------------
  * Batched segmentation.  The paper segments one grid at a time; a batch

@@ -35,7 +35,8 @@ __all__ = [
     "msc_batch_plan_kernels", "msc_batch_plan_destroy", "msc_batch_autotune", "Batch",
     "Job", "Result", "JOB_SEGMENT", "JOB_CC_MASK", "msc_server_create", "msc_server_submit", "msc_server_poll",
     "msc_server_wait", "msc_server_release", "msc_server_stats", "msc_server_destroy", "Server",
-    "OP_ADJACENCY", "msc_adjacency_grid", "adjacency_grid",
+    "OP_ADJACENCY", "msc_adjacency_grid", "adjacency_grid", "OP_EXTREMUM_GRAPH", "msc_extremum_graph",
+    "extremum_graph",
 ]
 
 OK, ERR_ARG, ERR_WS, ERR_CUDA, ERR_NAN, ERR_NOT_CONVERGED, ERR_BUDGET, ERR_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
@@ -43,6 +44,7 @@ ERR_TOO_LARGE = -8
 NOALLOC_MAX_N = 1 << 22
 PENDING = 1
 OP_ORDER, OP_COMPRESS, OP_MS_ID, OP_SEGMENT, OP_CC_MASK, OP_CC_MESH, OP_ADJACENCY = 1, 2, 3, 4, 5, 6, 7
+OP_EXTREMUM_GRAPH = 8
 JOB_SEGMENT, JOB_CC_MASK = 1, 2
 
 
@@ -105,6 +107,7 @@ def load(build_if_missing: bool = False):
         "msc_cc_mask": (ctypes.c_int, [P, Grid, I32, P, P, SZ, P, P]),
         "msc_cc_mesh": (ctypes.c_int, [P, P, I32, P, P, SZ, P, P]),
         "msc_adjacency_grid": (ctypes.c_int, [P, Grid, I32, I32, P, P, I64, P, P, SZ, P, P]),
+        "msc_extremum_graph": (ctypes.c_int, [P, P, Grid, I32, I32, I32, P, P, P, I64, P, P, SZ, P, P]),
         "msc_launch_count": (ctypes.c_ulonglong, []),
         "msc_trace_enable": (None, [ctypes.c_int]),
         "msc_trace_reset": (None, []),
@@ -216,6 +219,12 @@ def msc_adjacency_grid(label, dims, conn, label_bound, a, b, cap, num_pairs, ws,
                        stream=None) -> int:
     return load().msc_adjacency_grid(_p(label), _grid(dims), conn, label_bound, _p(a), _p(b), cap, _p(num_pairs),
                                      _p(ws), ws_bytes, _p(status), _stream(stream))
+
+
+def msc_extremum_graph(label, order, dims, conn, label_bound, sense, a, b, saddle, cap, num_arcs, ws, ws_bytes,
+                       status, stream=None) -> int:
+    return load().msc_extremum_graph(_p(label), _p(order), _grid(dims), conn, label_bound, sense, _p(a), _p(b),
+                                     _p(saddle), cap, _p(num_arcs), _p(ws), ws_bytes, _p(status), _stream(stream))
 
 
 def msc_launch_count() -> int:
@@ -473,6 +482,35 @@ def adjacency_grid(label: torch.Tensor, dims, conn: int = 14, label_bound: int |
         K = int(k.item())
         if K <= cap:
             return a[:K], b[:K]
+        cap = K
+
+
+def extremum_graph(label: torch.Tensor, order_field: torch.Tensor, dims, sense: int = 1, conn: int = 14,
+                   label_bound: int | None = None, cap: int | None = None, ws: torch.Tensor | None = None):
+    """Arcs (a, b) of the extremum graph with their saddle vertices: pairs of
+    maximum (sense +1) or minimum (sense -1) regions that touch, in
+    lexicographic order, each with the end vertex of its highest (maxima) or
+    lowest (minima) crossing edge in the order.  Three int32 tensors."""
+    dev = _dev(label)
+    lab = _flat(label, torch.int32)
+    o = _flat(order_field, torch.int32)
+    n = lab.numel()
+    if n != int(dims[0]) * int(dims[1]) * int(dims[2]) or o.numel() != n:
+        raise MSCError(ERR_ARG, "extremum_graph: dims do not match the label / order size")
+    bound = max(n, 1) if label_bound is None else int(label_bound)
+    cap = min(7 * n, 1 << 24) if cap is None else int(cap)
+    if ws is None:
+        ws = _ws(OP_EXTREMUM_GRAPH, n, dev)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    k = torch.empty(1, dtype=torch.int64, device=dev)
+    while True:
+        a, b, s = (torch.empty(max(cap, 1), dtype=torch.int32, device=dev) for _ in range(3))
+        _check(msc_extremum_graph(lab, o, dims, conn, bound, sense, a, b, s, cap, k, ws, ws.numel(), st),
+               "msc_extremum_graph")
+        _finish(st, "msc_extremum_graph")
+        K = int(k.item())
+        if K <= cap:
+            return a[:K], b[:K], s[:K]
         cap = K
 
 

@@ -51,14 +51,33 @@ struct EmitArgs {
     int32_t* count;
     int64_t cap;  // entries of `out`
     int32_t* status;
+    // saddles (extremum graph): the vertex order, +1 for maximum labels or
+    // -1 for minimum labels, and the crossing vertex of each emitted key
+    const int32_t* order;
+    int sense;
+    int32_t* out_w;
 };
 
-__device__ __forceinline__ void append_global(const EmitArgs& a, unsigned long long key) {
+// A crossing vertex w at order level l as a value whose maximum is the
+// saddle: (l << 32 | w) for maxima (highest crossing), its complement for
+// minima (lowest crossing).  0 is below every value.
+__device__ __forceinline__ unsigned long long crossing_val(int sense, int32_t level, int32_t w) {
+    const unsigned long long p = (unsigned long long)(uint32_t)level << 32 | (uint32_t)w;
+    return sense > 0 ? p : ~p;
+}
+
+__device__ __forceinline__ int32_t crossing_vertex(int sense, unsigned long long val) {
+    return (int32_t)(uint32_t)(sense > 0 ? val : ~val);
+}
+
+__device__ __forceinline__ void append_global(const EmitArgs& a, unsigned long long key, unsigned long long val) {
     const uint32_t pos = atomicAdd(reinterpret_cast<uint32_t*>(a.count), 1u);
-    if ((int64_t)pos < a.cap)
+    if ((int64_t)pos < a.cap) {
         a.out[pos] = key;
-    else
+        if (a.out_w) a.out_w[pos] = crossing_vertex(a.sense, val);
+    } else {
         record_error(a.status, MSC_ERR_INTERNAL);  // more keys than edges: impossible
+    }
 }
 
 // Key of the pair of labels c and m, or kNoKey when m < 0.
@@ -75,34 +94,49 @@ __device__ __forceinline__ uint32_t set_home(unsigned long long key) {
     return h >> (32 - kSetBits);
 }
 
-// Inserts `key` (kNoKey = nothing) into the tile's shared set.  Called by
-// the whole warp; records new slots in s_used with one shared atomic per
-// warp.
-__device__ __forceinline__ void set_insert(const EmitArgs& a, unsigned long long key, unsigned long long* s_set,
-                                           uint16_t* s_used, uint32_t* s_nused, int lane) {
+// Inserts `key` (kNoKey = nothing) into the tile's shared set; with
+// SADDLE, also raises the key's value to `val`.  Called by the whole warp;
+// records new slots in s_used with one shared atomic per warp.
+template <bool SADDLE>
+__device__ __forceinline__ void set_insert(const EmitArgs& a, unsigned long long key, unsigned long long val,
+                                           unsigned long long* s_set, unsigned long long* s_val, uint16_t* s_used,
+                                           uint32_t* s_nused, int lane) {
+    if constexpr (SADDLE) {
+        // the first lane of a run of equal keys carries the run's maximum
+        // (lanes further on with the same key only add to the same maximum)
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const unsigned long long k2 = __shfl_down_sync(0xffffffffu, key, o);
+            const unsigned long long v2 = __shfl_down_sync(0xffffffffu, val, o);
+            if (lane + o < 32 && k2 == key && v2 > val) val = v2;
+        }
+    }
     // a boundary usually crosses neighbouring lanes with the same pair
     const unsigned long long prev = __shfl_up_sync(0xffffffffu, key, 1);
     int new_slot = -1;
     if (key != kNoKey && !(lane > 0 && prev == key)) {
         uint32_t h = set_home(key);
-        bool placed = false;
+        int slot = -1;
         for (int p = 0; p < kProbes; ++p) {
             const unsigned long long cur = s_set[h];
             if (cur == key) {
-                placed = true;
+                slot = (int)h;
                 break;
             }
             if (cur == kNoKey) {
                 const unsigned long long old = atomicCAS(&s_set[h], kNoKey, key);
                 if (old == kNoKey) new_slot = (int)h;
                 if (old == kNoKey || old == key) {
-                    placed = true;
+                    slot = (int)h;
                     break;
                 }
             }
             h = (h + 1) & (kSetSlots - 1);
         }
-        if (!placed) append_global(a, key);
+        if (slot < 0)
+            append_global(a, key, val);
+        else if constexpr (SADDLE)
+            atomicMax(&s_val[slot], val);
     }
     const uint32_t fresh = __ballot_sync(0xffffffffu, new_slot >= 0);
     if (fresh) {
@@ -147,11 +181,13 @@ __device__ __forceinline__ int32_t checked(const EmitArgs& a, int32_t l) {
 }
 
 // Called by the whole CTA: when `force` or the set holds a quarter of its
-// slots, appends the set's keys to the global buffer (one atomic) and
-// empties the set.  Returns the planes to the next check (the same in every
-// thread): few when the set is filling, more when it stayed nearly empty.
-__device__ __forceinline__ int flush_set(const EmitArgs& a, unsigned long long* s_set, const uint16_t* s_used,
-                                      uint32_t* s_nused, uint32_t* s_base, bool force) {
+// slots, appends the set's keys (and crossing vertices) to the global
+// buffer (one atomic) and empties the set.  Returns the planes to the next
+// check (the same in every thread): few when the set is filling, more when
+// it stayed nearly empty.
+template <bool SADDLE>
+__device__ __forceinline__ int flush_set(const EmitArgs& a, unsigned long long* s_set, unsigned long long* s_val,
+                                         const uint16_t* s_used, uint32_t* s_nused, uint32_t* s_base, bool force) {
     const int tid = threadIdx.x;
     const bool go = __syncthreads_or(force || (tid == 0 && *s_nused >= kSetSlots / 4));
     const uint32_t nu = *s_nused;  // every insert is behind the barrier above
@@ -169,11 +205,14 @@ __device__ __forceinline__ int flush_set(const EmitArgs& a, unsigned long long* 
     for (uint32_t i = tid; i < nu; i += kThreads) {
         const uint32_t slot = s_used[i];
         const uint32_t pos = *s_base + i;
-        if ((int64_t)pos < a.cap)
+        if ((int64_t)pos < a.cap) {
             a.out[pos] = s_set[slot];
-        else
+            if constexpr (SADDLE) a.out_w[pos] = crossing_vertex(a.sense, s_val[slot]);
+        } else {
             record_error(a.status, MSC_ERR_INTERNAL);
+        }
         s_set[slot] = kNoKey;  // cleared for the keys that follow
+        if constexpr (SADDLE) s_val[slot] = 0;
     }
     __syncthreads();
     return next;
@@ -185,13 +224,32 @@ __device__ __forceinline__ int flush_set(const EmitArgs& a, unsigned long long* 
 // x from a lane shuffle, in y from the row above, which L2 serves to both
 // warps that read it), so every label comes from DRAM about once and the
 // only barriers are the set's fill checks.
-template <int HALF>
+// Offset k of the link as a vertex-id difference.
+__device__ __forceinline__ int32_t offset_id(const EmitArgs& a, int k) {
+    const int dx = k == 0 || k == 3 || k == 4 || k == 6, dy = k == 1 || k == 3 || k == 5 || k == 6;
+    const int dz = k == 2 || k == 4 || k == 5 || k == 6;
+    return dx + a.nx * (dy + a.ny * dz);
+}
+
+// Shared memory of k_adj_emit: the set's keys, (SADDLE) their values, the
+// list of used slots.
+template <bool SADDLE>
+constexpr size_t emit_smem_bytes() {
+    return (size_t)kSetSlots * (sizeof(unsigned long long) * (SADDLE ? 2 : 1) + sizeof(uint16_t));
+}
+
+template <int HALF, bool SADDLE>
 __global__ void __launch_bounds__(kThreads) k_adj_emit(const EmitArgs a) {
-    __shared__ unsigned long long s_set[kSetSlots];
-    __shared__ uint16_t s_used[kSetSlots];
+    extern __shared__ __align__(16) unsigned long long emit_smem[];
+    unsigned long long* s_set = emit_smem;
+    unsigned long long* s_val = emit_smem + kSetSlots;  // SADDLE only
+    uint16_t* s_used = reinterpret_cast<uint16_t*>(emit_smem + kSetSlots * (SADDLE ? 2 : 1));
     __shared__ uint32_t s_nused, s_base;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    for (int i = tid; i < kSetSlots; i += kThreads) s_set[i] = kNoKey;
+    for (int i = tid; i < kSetSlots; i += kThreads) {
+        s_set[i] = kNoKey;
+        if constexpr (SADDLE) s_val[i] = 0;
+    }
     if (tid == 0) s_nused = 0;
     __syncthreads();
     // tile counts fit 32 bits: n < 2^31 vertices and every tile holds one
@@ -238,17 +296,35 @@ __global__ void __launch_bounds__(kThreads) k_adj_emit(const EmitArgs a) {
                 // meet; offsets with a third or later one go to `extra`
                 int32_t m0 = -1, m1 = -1;
                 uint32_t extra = 0;
+                // SADDLE: the best crossing towards m0 and m1 and per offset
+                unsigned long long v0 = 0, v1 = 0, vk[7] = {0, 0, 0, 0, 0, 0, 0};
                 if (c0 >= 0) {
+                    const int32_t v = x + a.nx * (y + a.ny * z);
+                    const int32_t ov = SADDLE ? __ldg(a.order + v) : 0;
 #pragma unroll
                     for (int k = 0; k < HALF; ++k) {
                         const int32_t m = nb[k];
-                        if (m >= 0 && m != c0 && m != m0 && m != m1) {
-                            if (m0 < 0)
-                                m0 = m;
-                            else if (m1 < 0)
-                                m1 = m;
-                            else
-                                extra |= 1u << k;
+                        if (m >= 0 && m != c0) {
+                            if constexpr (SADDLE) {
+                                // the crossing vertex of edge (v, u): the lower end
+                                // for maxima, the higher for minima
+                                const int32_t u = v + offset_id(a, k), ou = __ldg(a.order + u);
+                                const bool u_is = a.sense > 0 ? ou < ov : ou > ov;
+                                vk[k] = crossing_val(a.sense, u_is ? ou : ov, u_is ? u : v);
+                                if (m == m0) v0 = max(v0, vk[k]);
+                                if (m == m1) v1 = max(v1, vk[k]);
+                            }
+                            if (m != m0 && m != m1) {
+                                if (m0 < 0) {
+                                    m0 = m;
+                                    v0 = vk[k];
+                                } else if (m1 < 0) {
+                                    m1 = m;
+                                    v1 = vk[k];
+                                } else {
+                                    extra |= 1u << k;
+                                }
+                            }
                         }
                     }
                 }
@@ -258,10 +334,13 @@ __global__ void __launch_bounds__(kThreads) k_adj_emit(const EmitArgs a) {
                 const bool two = __any_sync(0xffffffffu, m1 >= 0);
                 for (int round = 0;; ++round) {
                     int32_t m;
+                    unsigned long long val = 0;
                     if (round == 0) {
                         m = m0;
+                        val = v0;
                     } else if (round == 1 && two) {
                         m = m1;
+                        val = v1;
                     } else {
                         if (!wextra) break;
                         const int k = __ffs(wextra) - 1;
@@ -269,8 +348,11 @@ __global__ void __launch_bounds__(kThreads) k_adj_emit(const EmitArgs a) {
                         m = extra >> k & 1u ? (k == 0 ? nb[0] : k == 1 ? nb[1] : k == 2 ? nb[2] : k == 3 ? nb[3]
                                                : k == 4 ? nb[4] : k == 5 ? nb[5] : nb[6])
                                             : -1;
+                        if constexpr (SADDLE)
+                            val = k == 0 ? vk[0] : k == 1 ? vk[1] : k == 2 ? vk[2] : k == 3 ? vk[3]
+                                : k == 4 ? vk[4] : k == 5 ? vk[5] : vk[6];
                     }
-                    set_insert(a, pair_key(a, c0, m), s_set, s_used, &s_nused, lane);
+                    set_insert<SADDLE>(a, pair_key(a, c0, m), val, s_set, s_val, s_used, &s_nused, lane);
                 }
             }
             cur = nx1;
@@ -282,7 +364,7 @@ __global__ void __launch_bounds__(kThreads) k_adj_emit(const EmitArgs a) {
             // keys that find no slot go out on their own), and at the
             // tile's end
             const bool last = z + 1 == ze;
-            if (--until == 0 || last) until = flush_set(a, s_set, s_used, &s_nused, &s_base, last);
+            if (--until == 0 || last) until = flush_set<SADDLE>(a, s_set, s_val, s_used, &s_nused, &s_base, last);
         }
     }
 }
@@ -360,10 +442,16 @@ __global__ void __launch_bounds__(1024) k_adj_scan(uint32_t* chunk_heads, const 
 // b = key & (2^shift - 1); ranks at or beyond `out_cap` are dropped.  The
 // chunk goes in kPer rounds of one key per thread (coalesced); a round's
 // ranks come from a block-wide count of the heads before each thread.
+// SADDLE: every key (head or not) also raises the value of its run's rank
+// in `best` to its crossing vertex's value (a warp first combines the
+// lanes of one run).
+template <bool SADDLE>
 __global__ void __launch_bounds__(kThreads) k_adj_write(const unsigned long long* __restrict__ keys,
                                                         const int32_t* d_count, int64_t cap,
                                                         const uint32_t* __restrict__ chunk_base, int shift,
-                                                        int32_t* out_a, int32_t* out_b, int64_t out_cap) {
+                                                        int32_t* out_a, int32_t* out_b, int64_t out_cap,
+                                                        const int32_t* __restrict__ cross, const int32_t* __restrict__ order,
+                                                        int sense, unsigned long long* best) {
     __shared__ uint32_t s_w[kThreads / 32];
     const int64_t m = clamp_count(d_count, cap);
     const int64_t nchunks = (m + kChunk - 1) / kChunk;
@@ -393,10 +481,43 @@ __global__ void __launch_bounds__(kThreads) k_adj_write(const unsigned long long
                 out_a[r] = (int32_t)(k >> shift);
                 out_b[r] = (int32_t)(k & mask);
             }
+            if constexpr (SADDLE) {
+                // rank of this key's run: the heads up to and including it, less one
+                const int64_t rr = r + (head ? 0 : -1);
+                unsigned long long val = 0;
+                if (i < m) {
+                    const int32_t w = cross[i];
+                    val = crossing_val(sense, __ldg(order + w), w);
+                }
+                int64_t rk = i < m ? rr : -1 - lane;  // lanes past the end never match
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const unsigned long long v2 = __shfl_down_sync(0xffffffffu, val, o);
+                    const int64_t r2 = __shfl_down_sync(0xffffffffu, rk, o);
+                    if (lane + o < 32 && r2 == rk && v2 > val) val = v2;
+                }
+                const int64_t rprev = __shfl_up_sync(0xffffffffu, rk, 1);
+                if (i < m && (lane == 0 || rprev != rk)) atomicMax(&best[rk], val);
+            }
             run += total;
             __syncthreads();  // s_w is rewritten by the next round
         }
     }
+}
+
+// best[0 .. K) = 0 (K distinct pairs, read on the device).
+__global__ void k_adj_zero(unsigned long long* best, const int64_t* num_pairs) {
+    const int64_t k = *num_pairs;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+        best[i] = 0ull;
+}
+
+// saddle[r] = the crossing vertex held in best[r], r < min(K, out_cap).
+__global__ void k_adj_saddle(const unsigned long long* __restrict__ best, const int64_t* num_pairs, int sense,
+                             int32_t* saddle, int64_t out_cap) {
+    const int64_t k = min(*num_pairs, out_cap);
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < k; i += (int64_t)gridDim.x * blockDim.x)
+        saddle[i] = crossing_vertex(sense, best[i]);
 }
 
 int64_t emit_capacity(int64_t n) { return 7 * std::max<int64_t>(n, 1); }
@@ -409,45 +530,63 @@ int blocks_for(int64_t work, int per_sm) {
 
 bool adjacency_size_ok(int64_t n) { return n >= 0 && emit_capacity(n) <= (int64_t)INT32_MAX; }
 
-void size_adjacency_scratch(Sizer& s, int64_t n) {
+void size_adjacency_scratch(Sizer& s, int64_t n, bool saddle) {
     const int64_t cap = emit_capacity(n);
     s.take<int32_t>(64);
     s.take<unsigned long long>(cap);
     s.take<unsigned long long>(cap);
+    if (saddle) {
+        s.take<int32_t>(cap);
+        s.take<int32_t>(cap);
+    }
     s.take<uint32_t>(ceil_div(cap, kChunk) + 1);
     size_sort_scratch(s, cap);
 }
 
+template <bool SADDLE>
+static int launch_emit(const EmitArgs& ea, int conn, int64_t tiles, cudaStream_t s) {
+    auto kern = conn == 6 ? k_adj_emit<3, SADDLE> : k_adj_emit<7, SADDLE>;
+    constexpr size_t smem = emit_smem_bytes<SADDLE>();
+    MSC_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    // persistent: as many CTAs as fit on the GPU at once
+    int occ = 0;
+    MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, smem));
+    {
+        TraceScope ts_("adjacency.emit", s);
+        kern<<<blocks_for(tiles, std::max(occ, 1)), kThreads, smem, s>>>(ea);
+    }
+    MSC_LAUNCHED();
+    return MSC_OK;
+}
+
 int run_adjacency_grid(const int32_t* label, msc_grid g, int conn, int32_t bound, int32_t* out_a,
                        int32_t* out_b, int64_t out_cap, int64_t* num_pairs, void* ws, size_t ws_bytes,
-                       int32_t* status, cudaStream_t s) {
+                       int32_t* status, cudaStream_t s, const int32_t* order, int sense, int32_t* saddle) {
+    const bool with_saddle = order != nullptr;
     const int64_t n = (int64_t)g.nx * g.ny * g.nz;
     const int64_t cap = emit_capacity(n);
     Carver c(ws, ws_bytes);
     int32_t* ctl = c.take<int32_t>(64);
     unsigned long long* k0 = c.take<unsigned long long>(cap);
     unsigned long long* k1 = c.take<unsigned long long>(cap);
+    int32_t* w0 = with_saddle ? c.take<int32_t>(cap) : nullptr;
+    int32_t* w1 = with_saddle ? c.take<int32_t>(cap) : nullptr;
     uint32_t* chunk = c.take<uint32_t>(ceil_div(cap, kChunk) + 1);
     SortScratch sc = carve_sort_scratch(c, cap);
     if (!c.ok()) return MSC_ERR_WS;
     MSC_TRY(cudaMemsetAsync(ctl, 0, 64 * sizeof(int32_t), s));
     const int shift = ceil_log2(bound);
-    EmitArgs ea{label, g.nx, g.ny, g.nz, bound, shift, k0, ctl, cap, status};
+    const EmitArgs ea{label, g.nx, g.ny, g.nz, bound, shift, k0, ctl, cap, status, order, sense, w0};
     const int64_t tiles = ceil_div(g.nx, kTX) * ceil_div(g.ny, kTY) * ceil_div(g.nz, kZR);
-    {
-        TraceScope ts_("adjacency.emit", s);
-        // persistent: as many CTAs as fit on the GPU at once
-        auto kern = conn == 6 ? k_adj_emit<3> : k_adj_emit<7>;
-        int occ = 0;
-        MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
-        kern<<<blocks_for(tiles, std::max(occ, 1)), kThreads, 0, s>>>(ea);
-    }
-    MSC_LAUNCHED();
+    int r = with_saddle ? launch_emit<true>(ea, conn, tiles, s) : launch_emit<false>(ea, conn, tiles, s);
+    if (r) return r;
     bool in_alt = false;
-    int r = run_sort_u64(k0, nullptr, k1, nullptr, ctl, cap, 2 * shift, sc, status, s, &in_alt,
-                         "adjacency.sort_hist", "adjacency.sort_pass");
+    r = run_sort_u64(k0, w0, k1, w1, ctl, cap, 2 * shift, sc, status, s, &in_alt, "adjacency.sort_hist",
+                     "adjacency.sort_pass");
     if (r) return r;
     const unsigned long long* sorted = in_alt ? k1 : k0;
+    const int32_t* cross = in_alt ? w1 : w0;
+    unsigned long long* best = in_alt ? k0 : k1;  // the other key buffer is free now
     const int grid = blocks_for(ceil_div(cap, kChunk), 8);
     {
         TraceScope ts_("adjacency.heads", s);
@@ -459,11 +598,32 @@ int run_adjacency_grid(const int32_t* label, msc_grid g, int conn, int32_t bound
         k_adj_scan<<<1, 1024, 0, s>>>(chunk, ctl, cap, num_pairs);
     }
     MSC_LAUNCHED();
-    {
-        TraceScope ts_("adjacency.write", s);
-        k_adj_write<<<grid, kThreads, 0, s>>>(sorted, ctl, cap, chunk, shift, out_a, out_b, out_cap);
+    if (with_saddle) {
+        {
+            TraceScope ts_("adjacency.zero", s);
+            k_adj_zero<<<blocks_for(ceil_div(cap, kThreads), 8), kThreads, 0, s>>>(best, num_pairs);
+        }
+        MSC_LAUNCHED();
+        {
+            TraceScope ts_("adjacency.write", s);
+            k_adj_write<true><<<grid, kThreads, 0, s>>>(sorted, ctl, cap, chunk, shift, out_a, out_b, out_cap,
+                                                        cross, order, sense, best);
+        }
+        MSC_LAUNCHED();
+        {
+            TraceScope ts_("adjacency.saddle", s);
+            k_adj_saddle<<<blocks_for(ceil_div(cap, kThreads), 8), kThreads, 0, s>>>(best, num_pairs, sense,
+                                                                                     saddle, out_cap);
+        }
+        MSC_LAUNCHED();
+    } else {
+        {
+            TraceScope ts_("adjacency.write", s);
+            k_adj_write<false><<<grid, kThreads, 0, s>>>(sorted, ctl, cap, chunk, shift, out_a, out_b, out_cap,
+                                                         nullptr, nullptr, 0, nullptr);
+        }
+        MSC_LAUNCHED();
     }
-    MSC_LAUNCHED();
     return MSC_OK;
 }
 

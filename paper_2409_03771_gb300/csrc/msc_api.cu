@@ -142,8 +142,9 @@ size_t msc_workspace_bytes(int op, int64_t n, int64_t nnz) {
         case MSC_OP_CC_MASK: return 256;
         case MSC_OP_CC_MESH: return 256;
         case MSC_OP_ADJACENCY:
+        case MSC_OP_EXTREMUM_GRAPH:
             if (!adjacency_size_ok(n)) return 0;
-            size_adjacency_scratch(s, n);
+            size_adjacency_scratch(s, n, op == MSC_OP_EXTREMUM_GRAPH);
             return s.used;
         default: return 0;
     }
@@ -283,6 +284,22 @@ int msc_adjacency_grid(const int32_t* label, msc_grid g, int32_t conn, int32_t l
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
     return run_adjacency_grid(label, g, conn, label_bound, a, b, cap, num_pairs, ws, ws_bytes, d_status, s);
+}
+
+int msc_extremum_graph(const int32_t* label, const int32_t* order, msc_grid g, int32_t conn, int32_t label_bound,
+                       int32_t sense, int32_t* a, int32_t* b, int32_t* saddle, int64_t cap, int64_t* num_arcs,
+                       void* ws, size_t ws_bytes, int32_t* d_status, void* stream) {
+    if (!grid_ok(g) || !label || !order || !num_arcs || !d_status || !ws || !ws_aligned(ws) ||
+        (conn != 6 && conn != 14) || (sense != 1 && sense != -1) || label_bound <= 0 || cap < 0 ||
+        (cap > 0 && (!a || !b || !saddle)))
+        return MSC_ERR_ARG;
+    const int64_t n = grid_n(g);
+    if (!adjacency_size_ok(n)) return MSC_ERR_TOO_LARGE;
+    if (ws_bytes < msc_workspace_bytes(MSC_OP_EXTREMUM_GRAPH, n, 0)) return MSC_ERR_WS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
+    return run_adjacency_grid(label, g, conn, label_bound, a, b, cap, num_arcs, ws, ws_bytes, d_status, s, order,
+                              sense, saddle);
 }
 
 }  // extern "C"

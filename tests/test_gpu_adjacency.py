@@ -180,3 +180,131 @@ def test_full_size_512(m, kind):
         assert torch.equal(got, want)
         del a, b, want, got
         torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# extremum graph: arcs with their saddles (msc_extremum_graph)
+
+
+def check_graph(m, oracle_mod, lab, order, dims, conn, sense, bound=None):
+    lab = np.ascontiguousarray(lab, dtype=np.int32)
+    order = np.ascontiguousarray(order, dtype=np.int32)
+    wa, wb, ws = oracle_mod.extremum_graph(lab, order, dims, conn, sense)
+    a, b, s = m.extremum_graph(torch.as_tensor(lab).cuda(), torch.as_tensor(order).cuda(), dims, sense, conn,
+                               label_bound=bound)
+    np.testing.assert_array_equal(a.cpu().numpy(), wa)
+    np.testing.assert_array_equal(b.cpu().numpy(), wb)
+    np.testing.assert_array_equal(s.cpu().numpy(), ws)
+    return wa.size
+
+
+@pytest.mark.parametrize("sense", [1, -1])
+@pytest.mark.parametrize("conn", [6, 14])
+@pytest.mark.parametrize("dims", [(70, 19, 11), (33, 9, 40), (5, 3, 70)])
+def test_graph_random_labels_and_orders(m, oracle_mod, dims, conn, sense):
+    rng = np.random.default_rng(dims[2] + conn + sense)
+    n = dims[0] * dims[1] * dims[2]
+    lab = rng.integers(-1, 30, n).astype(np.int32)
+    order = rng.permutation(n).astype(np.int32)
+    assert check_graph(m, oracle_mod, lab, order, dims, conn, sense, bound=30) > 50
+
+
+@pytest.mark.parametrize("kind,edge", [("smooth", 64), ("noise", 40)])
+def test_graph_of_segmentations(m, oracle_mod, kind, edge):
+    """Maxima joined through their highest boundary crossing and minima
+    through their lowest, for the oracle's own segmentations."""
+    dims = (edge, edge + 3, edge - 5)
+    if kind == "smooth":
+        f = workloads.smooth_field(dims, 12, (3.0, 9.0), seed=4).reshape(-1).numpy()
+    else:
+        f = workloads.white_noise(dims, seed=4).reshape(-1).numpy()
+    order, asc, desc, ms, cells = oracle_mod.segment_grid(f, dims)
+    for conn in (14, 6):
+        assert check_graph(m, oracle_mod, desc, order, dims, conn, 1) > 0
+        assert check_graph(m, oracle_mod, asc, order, dims, conn, -1) > 0
+
+
+def test_graph_on_a_line(m, oracle_mod):
+    dims = (1, 1, 300)
+    f = np.random.default_rng(5).permutation(300).astype(np.float32)
+    order, asc, desc, ms, cells = oracle_mod.segment_grid(f, dims)
+    assert check_graph(m, oracle_mod, desc, order, dims, 14, 1) > 10
+    assert check_graph(m, oracle_mod, asc, order, dims, 6, -1) > 10
+
+
+def test_graph_capacity(m, oracle_mod):
+    dims = (50, 30, 20)
+    n = 30000
+    rng = np.random.default_rng(2)
+    lab = rng.integers(0, 200, n).astype(np.int32)
+    order = rng.permutation(n).astype(np.int32)
+    wa, wb, ws = oracle_mod.extremum_graph(lab, order, dims, 14, 1)
+    K = wa.size
+    d, o = torch.as_tensor(lab).cuda(), torch.as_tensor(order).cuda()
+    ws_t = torch.empty(m.msc_workspace_bytes(m.OP_EXTREMUM_GRAPH, n), dtype=torch.uint8, device="cuda")
+    st = torch.empty(1, dtype=torch.int32, device="cuda")
+    k = torch.empty(1, dtype=torch.int64, device="cuda")
+    for cap in (0, K // 2, K):
+        a, b, s = (torch.full((cap + 4,), -5, dtype=torch.int32, device="cuda") for _ in range(3))
+        assert m.msc_extremum_graph(d, o, dims, 14, 200, 1, a, b, s, cap, k, ws_t, ws_t.numel(), st) == m.OK
+        torch.cuda.synchronize()
+        assert int(st.item()) == m.OK and int(k.item()) == K
+        np.testing.assert_array_equal(s[:cap].cpu().numpy(), ws[:cap])
+        assert bool((s[cap:] == -5).all())
+
+
+def torch_graph(lab, order, dims, sense, shift):
+    """Plain PyTorch: per pair key, the best crossing (level << 32 | vertex)."""
+    nx, ny, nz = dims
+    L = lab.reshape(nz, ny, nx).long()
+    O = order.reshape(nz, ny, nx).long()
+    ids = torch.arange(nx * ny * nz, device=lab.device).reshape(nz, ny, nx)
+    keys, vals = [], []
+    for dx, dy, dz in POS:
+        sl_a = (slice(0, nz - dz), slice(0, ny - dy), slice(0, nx - dx))
+        sl_b = (slice(dz, nz), slice(dy, ny), slice(dx, nx))
+        A, B = L[sl_a], L[sl_b]
+        on = (A >= 0) & (B >= 0) & (A != B)
+        oa, ob = O[sl_a][on], O[sl_b][on]
+        ia, ib = ids[sl_a][on], ids[sl_b][on]
+        pick_a = (oa < ob) if sense > 0 else (oa > ob)
+        lev = torch.where(pick_a, oa, ob)
+        w = torch.where(pick_a, ia, ib)
+        v = (lev << 32) | w
+        keys.append((torch.minimum(A, B)[on] << shift) | torch.maximum(A, B)[on])
+        vals.append(v if sense > 0 else -v)  # the minimum crossing as a maximum
+        del A, B, on, oa, ob, ia, ib, pick_a, lev, w, v
+    keys = torch.cat(keys)
+    vals = torch.cat(vals)
+    uk, inv = torch.unique(keys, return_inverse=True)
+    best = torch.full((uk.numel(),), torch.iinfo(torch.int64).min, dtype=torch.int64, device=lab.device)
+    best.scatter_reduce_(0, inv, vals, reduce="amax")
+    if sense < 0:
+        best = -best
+    return uk, (best & 0xFFFFFFFF)
+
+
+def test_graph_full_size_512(m):
+    """512^3 smooth and noise fields: maxima arcs and saddles equal plain
+    PyTorch group-by over every edge; minima arcs on the smooth field."""
+    E = 512
+    dims = (E, E, E)
+    n = E ** 3
+    for kind, senses in (("smooth", (1, -1)), ("noise", (1,))):
+        f = (workloads.field_smooth(edge=E, seed=1, device="cuda") if kind == "smooth"
+             else workloads.field_noise(edge=E, seed=1, device="cuda")).reshape(-1)
+        order, asc, desc, ms, cells = m.segment(f, dims)
+        del ms, f
+        torch.cuda.empty_cache()
+        for sense in senses:
+            lab = desc if sense > 0 else asc
+            shift = max(int(n - 1).bit_length(), 0)
+            a, b, s = m.extremum_graph(lab, order, dims, sense)
+            uk, w = torch_graph(lab, order, dims, sense, shift)
+            assert a.numel() == uk.numel()
+            assert torch.equal((a.long() << shift) | b.long(), uk)
+            assert torch.equal(s.long(), w)
+            del a, b, s, uk, w
+            torch.cuda.empty_cache()
+        del order, asc, desc
+        torch.cuda.empty_cache()

@@ -85,6 +85,14 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert m.msc_adjacency_grid(16, (4, 4, 4), 14, 64, **dict(args, ws=256 + 8)) == m.ERR_ARG
     assert m.msc_adjacency_grid(16, (4, 4, 4), 14, 64, **dict(args, ws_bytes=ws - 1)) == m.ERR_WS
     assert m.msc_adjacency_grid(16, (1024, 1024, 1024), 6, 64, **args) == m.ERR_TOO_LARGE
+    # extremum graph: the order is required, sense is +1 or -1, the saddle output is needed
+    gws = m.msc_workspace_bytes(m.OP_EXTREMUM_GRAPH, 64)
+    assert gws > ws
+    gargs = dict(a=16, b=16, saddle=16, cap=4, num_arcs=16, ws=256, ws_bytes=gws, status=16, stream=0)
+    assert m.msc_extremum_graph(16, 0, (4, 4, 4), 14, 64, 1, **gargs) == m.ERR_ARG
+    assert m.msc_extremum_graph(16, 16, (4, 4, 4), 14, 64, 0, **gargs) == m.ERR_ARG
+    assert m.msc_extremum_graph(16, 16, (4, 4, 4), 14, 64, 1, **dict(gargs, saddle=0)) == m.ERR_ARG
+    assert m.msc_extremum_graph(16, 16, (4, 4, 4), 14, 64, -1, **dict(gargs, ws_bytes=ws)) == m.ERR_WS
 
 
 def test_no_cpu_fallback():
