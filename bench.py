@@ -49,6 +49,7 @@ def parse_args():
     ap.add_argument("--serve-requests", type=int, default=64, help="requests per arrival rate")
     ap.add_argument("--no-density", action="store_true", help="skip the 1024^3 mask-density sweep")
     ap.add_argument("--no-adjacency", action="store_true", help="skip the region-adjacency measurement")
+    ap.add_argument("--copy-streams", type=int, default=1, help="copy streams per direction in the e2e leg")
     return ap.parse_args()
 
 
@@ -305,10 +306,13 @@ def run_ours(args):
 
     # ---- end to end: pinned host inputs in, every output back to host ----
     # Pipelined as a user of the streams API would run it: the inputs of a
-    # step go in on one stream, the step computes on another, its outputs
-    # come back on a third; inputs and outputs are double-buffered, so the
-    # copies of neighbouring steps overlap the compute.  Every step still
-    # copies all its inputs in and all its outputs out.
+    # step go in on copy streams, the step computes on its own stream, its
+    # outputs come back on other copy streams; inputs and outputs are
+    # double-buffered, so the copies of neighbouring steps overlap the
+    # compute.  Each direction's copies are cut into pieces of at most
+    # 64 MiB dealt round-robin over --copy-streams streams, so that several
+    # copy engines work at once.  Every step still copies all its inputs in
+    # and all its outputs out.
     e2e = None
     if not args.no_e2e:
         srcs = (f_smooth, f_noise, mask, row, col)
@@ -324,29 +328,45 @@ def run_ours(args):
         h_out = [[torch.empty(x.shape, dtype=x.dtype, pin_memory=True) for x in flat(d_out[0])] for _ in range(2)]
         h2d = sum(x.numel() * x.element_size() for x in h_in)
         d2h = sum(x.numel() * x.element_size() for x in h_out[0])
-        s_in, s_out = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
-        ev_in = [torch.cuda.Event() for _ in range(2)]
+        ncs = max(1, args.copy_streams)
+        s_in = [torch.cuda.Stream(dev) for _ in range(ncs)]
+        s_out = [torch.cuda.Stream(dev) for _ in range(ncs)]
+        ev_in = [[torch.cuda.Event() for _ in range(ncs)] for _ in range(2)]
         ev_done = [torch.cuda.Event() for _ in range(2)]
-        ev_out = [torch.cuda.Event() for _ in range(2)]
-        for e in ev_done + ev_out:
+        ev_out = [[torch.cuda.Event() for _ in range(ncs)] for _ in range(2)]
+        for e in ev_done + [x for xs in ev_out for x in xs]:
             e.record(stream)
+
+        def pieces(dsts, srcs_):
+            """(dst, src) views of at most 64 MiB covering every pair."""
+            out = []
+            for d, h in zip(dsts, srcs_):
+                d1, h1 = d.view(-1), h.view(-1)
+                step_elems = max(1, (64 << 20) // d1.element_size())
+                for a in range(0, d1.numel(), step_elems):
+                    out.append((d1[a:a + step_elems], h1[a:a + step_elems]))
+            return out
 
         def e2e_step(i):
             b = i % 2
-            s_in.wait_event(ev_done[b])  # step i-2 no longer reads d_in[b]
-            with torch.cuda.stream(s_in):
-                for d, h in zip(d_in[b], h_in):
+            for j in range(ncs):
+                s_in[j].wait_event(ev_done[b])  # step i-2 no longer reads d_in[b]
+            for j, (d, h) in enumerate(pieces(d_in[b], h_in)):
+                with torch.cuda.stream(s_in[j % ncs]):
                     d.copy_(h, non_blocking=True)
-            ev_in[b].record(s_in)
-            stream.wait_event(ev_in[b])
-            stream.wait_event(ev_out[b])  # step i-2's outputs in d_out[b] have left
+            for j in range(ncs):
+                ev_in[b][j].record(s_in[j])
+                stream.wait_event(ev_in[b][j])
+                stream.wait_event(ev_out[b][j])  # step i-2's outputs in d_out[b] have left
             step(*d_in[b], out=d_out[b], st=stream)
             ev_done[b].record(stream)
-            s_out.wait_event(ev_done[b])
-            with torch.cuda.stream(s_out):
-                for h, d in zip(h_out[b], flat(d_out[b])):
+            for j in range(ncs):
+                s_out[j].wait_event(ev_done[b])
+            for j, (h, d) in enumerate(pieces(h_out[b], flat(d_out[b]))):
+                with torch.cuda.stream(s_out[j % ncs]):
                     h.copy_(d, non_blocking=True)
-            ev_out[b].record(s_out)
+            for j in range(ncs):
+                ev_out[b][j].record(s_out[j])
 
         for i in range(2):
             e2e_step(i)
@@ -355,19 +375,22 @@ def run_ours(args):
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
-        s_in.wait_event(ev0)
+        for j in range(ncs):
+            s_in[j].wait_event(ev0)
         for i in range(ee):
             e2e_step(i)
         for b in range(2):
-            stream.wait_event(ev_out[b])
+            for j in range(ncs):
+                stream.wait_event(ev_out[b][j])
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
         check_status("e2e")
         e_ms, e_value = replica_throughput(ev0.elapsed_time(ev1) / ee, verts, world, dev)
         e2e = {"value": e_value, "unit": "vertices/s", "ms_per_step": e_ms, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h, "pipelined": "inputs, compute and outputs on three streams, "
-                                                      "double-buffered; every step copies all inputs and outputs"}
+               "d2h_bytes_per_step": d2h,
+               "pipelined": (f"inputs and outputs in pieces of <= 64 MiB over {ncs} copy streams per direction, "
+                             "compute on its own stream, double-buffered; every step copies all inputs and outputs")}
         del d_in, d_out, h_out
 
     # ---- rooflines (live trace over the timed region) ----
