@@ -70,7 +70,7 @@ def test_noalloc_rejects_sizes_beyond_its_scratch(m):
     ptr = torch.arange(n, dtype=torch.int32, device="cuda")
     st = torch.zeros(1, dtype=torch.int32, device="cuda")
     assert m.msc_compress_noalloc(ptr, n, st) == m.ERR_TOO_LARGE
-    assert "static scratch" in m.msc_status_string(m.ERR_TOO_LARGE)
+    assert "exceeds a limit" in m.msc_status_string(m.ERR_TOO_LARGE)
     # device-side errors still reach the status word
     cyc = torch.tensor([1, 2, 0], dtype=torch.int32, device="cuda")
     assert m.msc_compress_noalloc(cyc, 3, st) == m.OK
