@@ -140,27 +140,31 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
-def kernel_sources_sha():
+def sources_sha(names):
+    """Hash of the kernel source files `names` (in the package's csrc) and the
+    headers every kernel includes."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2409_03771_gb300", "csrc")
-    for f in sorted(os.listdir(csrc)):
+    for f in ["common.cuh", "tma.cuh"] + sorted(names):
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
+    with open(os.path.join(ROOT, "include", "msc.h"), "rb") as fh:
+        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
 def committed_traffic(label):
     """DRAM bytes per vertex of a kernel from a committed ncu summary, if the
-    kernel sources have not changed since it was taken."""
+    kernel's source file has not changed since it was taken."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
     if not os.path.exists(path):
         return None
     with open(path) as fh:
         t = json.load(fh)
-    if t.get("sources_sha") != kernel_sources_sha():
-        return None
     e = t.get("kernels", {}).get(label)
-    return None if e is None else float(e["dram_bytes_per_vertex"])
+    if e is None or e.get("sha") != sources_sha([e["source"]]):
+        return None
+    return float(e["dram_bytes_per_vertex"])
 
 
 def jump_activity(msc, fields, dims, dev):
