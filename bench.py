@@ -207,7 +207,7 @@ def algorithmic_bytes(label, n, nm, nnz):
         "cc.local": 5 * n,               # read mask, write label
         "cc.flatten": 8 * n,             # read label, write label
         "mesh.init": 4 * nm,             # write label = v
-        "mesh.link": 36 * nm,            # read row[v], row[v+1], two columns, three labels; write two hooks
+        "mesh.link": 24 * nm,            # read row[v], row[v+1], two columns, write two hooks
         "mesh.flatten": 8 * nm,          # read and write every label
         # mesh.hook reads only the edges of vertices outside the dominant
         # component: data-dependent, no fixed algorithmic figure

@@ -369,21 +369,18 @@ __global__ void k_mesh_init(int32_t* label, int32_t n) {
         label[v] = (int32_t)v;
 }
 
-// Unite every vertex with its first and second neighbour.  Both columns
-// come from one read of the row's start (they share a sector), so the CSR
-// is streamed once for the two links.
-__global__ void k_mesh_link(const int32_t* __restrict__ row, const int32_t* __restrict__ col, int32_t n,
-                            int32_t* label, int32_t* status) {
+// Unite every vertex with its k-th neighbour (k = 0 or 1).
+__global__ void k_mesh_link_k(const int32_t* __restrict__ row, const int32_t* __restrict__ col, int32_t n,
+                              int k, int32_t* label, int32_t* status) {
     for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < n; v += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t e = row[v], end = row[v + 1];
-        const int32_t u0 = e < end ? col[e] : (int32_t)v;
-        const int32_t u1 = e + 1 < end ? col[e + 1] : (int32_t)v;
-        if ((uint32_t)u0 >= (uint32_t)n || (uint32_t)u1 >= (uint32_t)n) {
+        const int32_t e = row[v] + k;
+        if (e >= row[v + 1]) continue;
+        const int32_t u = col[e];
+        if ((uint32_t)u >= (uint32_t)n) {
             record_error(status, MSC_ERR_ARG);
             continue;
         }
-        if (u0 != v) union_g(label, (int32_t)v, u0, status);
-        if (u1 != v) union_g(label, (int32_t)v, u1, status);
+        union_g(label, (int32_t)v, u, status);
     }
 }
 
@@ -501,9 +498,9 @@ int run_cc_mesh(const int32_t* row, const int32_t* col, int32_t n, int32_t* labe
         k_mesh_init<<<grid, 256, 0, s>>>(label, n);
     }
     MSC_LAUNCHED();
-    {
+    for (int k = 0; k < 2; ++k) {
         TraceScope ts_("mesh.link", s);
-        k_mesh_link<<<grid, 256, 0, s>>>(row, col, n, label, status);
+        k_mesh_link_k<<<grid, 256, 0, s>>>(row, col, n, k, label, status);
     }
     MSC_LAUNCHED();
     {
