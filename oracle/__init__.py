@@ -70,6 +70,7 @@ def _load():
             "oracle_cc_grid_at": (i32, [P, i32, i32, i32, i32, i64, P, P]),
             "oracle_adjacency_grid": (i32, [P, i32, i32, i32, i32, P, P, i64, P]),
             "oracle_extremum_graph": (i32, [P, P, i32, i32, i32, i32, i32, P, P, P, i64, P]),
+            "oracle_adjacency_csr": (i32, [P, P, P, P, i32, i32, P, P, P, i64, P]),
         }
         for name, (res, args) in sig.items():
             fn = getattr(lib, name)
@@ -253,3 +254,24 @@ def extremum_graph(label, order, dims, conn: int = 14, sense: int = 1):
     _check(_load().oracle_extremum_graph(_ptr(lab), _ptr(o), nx, ny, nz, conn, sense, _ptr(a), _ptr(b), _ptr(s), k,
                                          ctypes.byref(cnt)), "extremum_graph")
     return a[:k], b[:k], s[:k]
+
+
+def adjacency_csr(label, row, col, order=None, sense: int = 1):
+    """Over an explicit mesh (symmetric CSR): the distinct label pairs (a, b),
+    a < b, across its edges, and with `order` also each pair's saddle (the
+    crossing vertex of its highest (sense +1) or lowest (-1) edge).  Returns
+    (a, b) or (a, b, saddle)."""
+    lab = _c(label, np.int32).ravel()
+    r = _c(row, np.int32).ravel()
+    c = _c(col, np.int32).ravel() if np.asarray(col).size else np.zeros(1, np.int32)
+    o = None if order is None else _c(order, np.int32).ravel()
+    n = lab.size
+    cnt = ctypes.c_int64()
+    op = 0 if o is None else _ptr(o)
+    _check(_load().oracle_adjacency_csr(_ptr(lab), op, _ptr(r), _ptr(c), n, sense, 0, 0, 0, 0, ctypes.byref(cnt)),
+           "adjacency_csr")
+    k = cnt.value
+    a, b, s = (np.empty(max(k, 1), np.int32) for _ in range(3))
+    _check(_load().oracle_adjacency_csr(_ptr(lab), op, _ptr(r), _ptr(c), n, sense, _ptr(a), _ptr(b), _ptr(s), k,
+                                        ctypes.byref(cnt)), "adjacency_csr")
+    return (a[:k], b[:k]) if o is None else (a[:k], b[:k], s[:k])

@@ -633,3 +633,69 @@ int oracle_extremum_graph(const int32_t* label, const int32_t* order, int32_t nx
     *count = k;
     return OR_OK;
 }
+
+/* ------------------------------------------------------------------------ */
+/* The same two operations over an explicit mesh (the explicit-triangulation
+ * case): the edges are the CSR entries (row[n+1], col[row[n]]), symmetric;
+ * each edge is taken from the row of its smaller end.  order may be NULL
+ * for the plain adjacency; with order, saddle_out receives each pair's
+ * crossing vertex as in oracle_extremum_graph.                              */
+
+int oracle_adjacency_csr(const int32_t* label, const int32_t* order, const int32_t* row, const int32_t* col,
+                         int32_t n, int sense, int32_t* a_out, int32_t* b_out, int32_t* saddle_out, int64_t cap,
+                         int64_t* count) {
+    if (n < 0 || !label || !row || !col || !count || cap < 0 || (order && sense != 1 && sense != -1))
+        return OR_ERR_ARG;
+    int64_t m = 0, mcap = 1024;
+    or_arc* arcs = (or_arc*)malloc((size_t)mcap * sizeof(or_arc));
+    if (!arcs) return OR_ERR_OOM;
+    for (int32_t v = 0; v < n; ++v) {
+        for (int32_t e = row[v]; e < row[v + 1]; ++e) {
+            const int32_t u = col[e];
+            if (u < 0 || u >= n) {
+                free(arcs);
+                return OR_ERR_ARG;
+            }
+            if (u <= v) continue; /* each edge from its smaller end */
+            const int32_t la = label[v], lb = label[u];
+            if (la < 0 || lb < 0 || la == lb) continue;
+            if (m == mcap) {
+                mcap *= 2;
+                or_arc* p2 = (or_arc*)realloc(arcs, (size_t)mcap * sizeof(or_arc));
+                if (!p2) {
+                    free(arcs);
+                    return OR_ERR_OOM;
+                }
+                arcs = p2;
+            }
+            const uint32_t lo = (uint32_t)(la < lb ? la : lb), hi = (uint32_t)(la < lb ? lb : la);
+            arcs[m].key = ((uint64_t)lo << 32) | hi;
+            if (order) {
+                const int lower_is_v = order[v] < order[u];
+                const int32_t w = (sense > 0) == lower_is_v ? v : u;
+                arcs[m].level = order[w];
+                arcs[m].vertex = w;
+            } else {
+                arcs[m].level = 0;
+                arcs[m].vertex = 0;
+            }
+            ++m;
+        }
+    }
+    qsort(arcs, (size_t)m, sizeof(or_arc), or_cmp_arc);
+    int64_t k = 0;
+    for (int64_t i = 0; i < m; ++i) {
+        if (i > 0 && arcs[i].key == arcs[i - 1].key) continue;
+        int64_t j = i;
+        while (j + 1 < m && arcs[j + 1].key == arcs[i].key) ++j;
+        if (k < cap) {
+            a_out[k] = (int32_t)(arcs[i].key >> 32);
+            b_out[k] = (int32_t)(uint32_t)arcs[i].key;
+            if (order && saddle_out) saddle_out[k] = sense > 0 ? arcs[j].vertex : arcs[i].vertex;
+        }
+        ++k;
+    }
+    free(arcs);
+    *count = k;
+    return OR_OK;
+}
