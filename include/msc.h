@@ -72,11 +72,14 @@ enum {
     MSC_OP_CC_MASK = 5,
     MSC_OP_CC_MESH = 6,
     MSC_OP_ADJACENCY = 7,
-    MSC_OP_EXTREMUM_GRAPH = 8
+    MSC_OP_EXTREMUM_GRAPH = 8,
+    MSC_OP_ADJACENCY_CSR = 9,
+    MSC_OP_EXTREMUM_GRAPH_CSR = 10
 };
 
 /* Workspace bytes needed by `op` on n vertices (nnz CSR entries for
- * MSC_OP_CC_MESH, ignored otherwise).  0 for an unknown op or bad size. */
+ * MSC_OP_CC_MESH and the two *_CSR ops, ignored otherwise).  0 for an
+ * unknown op or bad size. */
 MSC_API size_t msc_workspace_bytes(int op, int64_t n, int64_t nnz);
 
 /* Human-readable name of a status code (static string). */
@@ -255,6 +258,27 @@ MSC_API int msc_extremum_graph(const int32_t* label, const int32_t* order, msc_g
                                int32_t label_bound, int32_t sense, int32_t* a, int32_t* b, int32_t* saddle,
                                int64_t cap, int64_t* num_arcs, void* ws, size_t ws_bytes, int32_t* d_status,
                                void* stream);
+
+/* The two operations above over an explicit mesh (the explicit
+ * triangulation case), whose edges are the entries of a symmetric CSR
+ * vertex adjacency, each taken from the row of its smaller end:
+ *   row, col   device int32 CSR: row[n+1], col[nnz], row[0] = 0,
+ *              row[n] = nnz.  A column outside [0, n) or a row range
+ *              outside [0, nnz] sets MSC_ERR_ARG in d_status.
+ *   nnz        the number of col entries (sizes the workspace; at most
+ *              2^31 - 1).
+ * Other arguments as for msc_adjacency_grid / msc_extremum_graph.
+ * Workspace: msc_workspace_bytes(MSC_OP_ADJACENCY_CSR or
+ * MSC_OP_EXTREMUM_GRAPH_CSR, n, nnz).
+ * Method: a lane per vertex, the warp stepping through its rows together;
+ * the keys (with their crossing vertices) are sorted and reduced as above. */
+MSC_API int msc_adjacency_csr(const int32_t* label, const int32_t* row, const int32_t* col, int32_t n, int64_t nnz,
+                              int32_t label_bound, int32_t* a, int32_t* b, int64_t cap, int64_t* num_pairs,
+                              void* ws, size_t ws_bytes, int32_t* d_status, void* stream);
+MSC_API int msc_extremum_graph_csr(const int32_t* label, const int32_t* order, const int32_t* row,
+                                   const int32_t* col, int32_t n, int64_t nnz, int32_t label_bound, int32_t sense,
+                                   int32_t* a, int32_t* b, int32_t* saddle, int64_t cap, int64_t* num_arcs,
+                                   void* ws, size_t ws_bytes, int32_t* d_status, void* stream);
 
 /* ---------------------------------------------------------------------
  * Batched segmentation.  The paper segments one grid at a time; a batch

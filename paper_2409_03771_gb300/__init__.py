@@ -36,7 +36,8 @@ __all__ = [
     "Job", "Result", "JOB_SEGMENT", "JOB_CC_MASK", "msc_server_create", "msc_server_submit", "msc_server_poll",
     "msc_server_wait", "msc_server_release", "msc_server_stats", "msc_server_destroy", "Server",
     "OP_ADJACENCY", "msc_adjacency_grid", "adjacency_grid", "OP_EXTREMUM_GRAPH", "msc_extremum_graph",
-    "extremum_graph",
+    "extremum_graph", "OP_ADJACENCY_CSR", "OP_EXTREMUM_GRAPH_CSR", "msc_adjacency_csr", "msc_extremum_graph_csr",
+    "adjacency_csr", "extremum_graph_csr",
 ]
 
 OK, ERR_ARG, ERR_WS, ERR_CUDA, ERR_NAN, ERR_NOT_CONVERGED, ERR_BUDGET, ERR_INTERNAL = 0, -1, -2, -3, -4, -5, -6, -7
@@ -44,7 +45,7 @@ ERR_TOO_LARGE = -8
 NOALLOC_MAX_N = 1 << 22
 PENDING = 1
 OP_ORDER, OP_COMPRESS, OP_MS_ID, OP_SEGMENT, OP_CC_MASK, OP_CC_MESH, OP_ADJACENCY = 1, 2, 3, 4, 5, 6, 7
-OP_EXTREMUM_GRAPH = 8
+OP_EXTREMUM_GRAPH, OP_ADJACENCY_CSR, OP_EXTREMUM_GRAPH_CSR = 8, 9, 10
 JOB_SEGMENT, JOB_CC_MASK = 1, 2
 
 
@@ -108,6 +109,8 @@ def load(build_if_missing: bool = False):
         "msc_cc_mesh": (ctypes.c_int, [P, P, I32, P, P, SZ, P, P]),
         "msc_adjacency_grid": (ctypes.c_int, [P, Grid, I32, I32, P, P, I64, P, P, SZ, P, P]),
         "msc_extremum_graph": (ctypes.c_int, [P, P, Grid, I32, I32, I32, P, P, P, I64, P, P, SZ, P, P]),
+        "msc_adjacency_csr": (ctypes.c_int, [P, P, P, I32, I64, I32, P, P, I64, P, P, SZ, P, P]),
+        "msc_extremum_graph_csr": (ctypes.c_int, [P, P, P, P, I32, I64, I32, I32, P, P, P, I64, P, P, SZ, P, P]),
         "msc_launch_count": (ctypes.c_ulonglong, []),
         "msc_trace_enable": (None, [ctypes.c_int]),
         "msc_trace_reset": (None, []),
@@ -225,6 +228,19 @@ def msc_extremum_graph(label, order, dims, conn, label_bound, sense, a, b, saddl
                        status, stream=None) -> int:
     return load().msc_extremum_graph(_p(label), _p(order), _grid(dims), conn, label_bound, sense, _p(a), _p(b),
                                      _p(saddle), cap, _p(num_arcs), _p(ws), ws_bytes, _p(status), _stream(stream))
+
+
+def msc_adjacency_csr(label, row, col, n, nnz, label_bound, a, b, cap, num_pairs, ws, ws_bytes, status,
+                      stream=None) -> int:
+    return load().msc_adjacency_csr(_p(label), _p(row), _p(col), n, nnz, label_bound, _p(a), _p(b), cap,
+                                    _p(num_pairs), _p(ws), ws_bytes, _p(status), _stream(stream))
+
+
+def msc_extremum_graph_csr(label, order, row, col, n, nnz, label_bound, sense, a, b, saddle, cap, num_arcs, ws,
+                           ws_bytes, status, stream=None) -> int:
+    return load().msc_extremum_graph_csr(_p(label), _p(order), _p(row), _p(col), n, nnz, label_bound, sense, _p(a),
+                                         _p(b), _p(saddle), cap, _p(num_arcs), _p(ws), ws_bytes, _p(status),
+                                         _stream(stream))
 
 
 def msc_launch_count() -> int:
@@ -512,6 +528,52 @@ def extremum_graph(label: torch.Tensor, order_field: torch.Tensor, dims, sense: 
         if K <= cap:
             return a[:K], b[:K], s[:K]
         cap = K
+
+
+def _csr_pairs(label, row, col, order, sense, label_bound, cap, ws):
+    dev = _dev(label)
+    lab = _flat(label, torch.int32)
+    row = _flat(row, torch.int32)
+    nnz = int(col.numel())
+    col = _cols(col)
+    n = lab.numel()
+    if row.numel() != n + 1:
+        raise MSCError(ERR_ARG, "CSR row array must have n + 1 entries")
+    o = None if order is None else _flat(order, torch.int32)
+    bound = max(n, 1) if label_bound is None else int(label_bound)
+    cap = min(max(nnz, 1), 1 << 24) if cap is None else int(cap)
+    op = OP_ADJACENCY_CSR if o is None else OP_EXTREMUM_GRAPH_CSR
+    if ws is None:
+        ws = _ws(op, n, dev, nnz)
+    st = torch.empty(1, dtype=torch.int32, device=dev)
+    k = torch.empty(1, dtype=torch.int64, device=dev)
+    while True:
+        a, b, s = (torch.empty(max(cap, 1), dtype=torch.int32, device=dev) for _ in range(3))
+        if o is None:
+            code = msc_adjacency_csr(lab, row, col, n, nnz, bound, a, b, cap, k, ws, ws.numel(), st)
+        else:
+            code = msc_extremum_graph_csr(lab, o, row, col, n, nnz, bound, sense, a, b, s, cap, k, ws, ws.numel(), st)
+        _check(code, "msc_adjacency_csr")
+        _finish(st, "msc_adjacency_csr")
+        K = int(k.item())
+        if K <= cap:
+            return (a[:K], b[:K]) if o is None else (a[:K], b[:K], s[:K])
+        cap = K
+
+
+def adjacency_csr(label: torch.Tensor, row: torch.Tensor, col: torch.Tensor, label_bound: int | None = None,
+                  cap: int | None = None, ws: torch.Tensor | None = None):
+    """Distinct label pairs (a, b), a < b, across the edges of a mesh given
+    as its symmetric CSR vertex adjacency: two int32 tensors."""
+    return _csr_pairs(label, row, col, None, 1, label_bound, cap, ws)
+
+
+def extremum_graph_csr(label: torch.Tensor, order_field: torch.Tensor, row: torch.Tensor, col: torch.Tensor,
+                       sense: int = 1, label_bound: int | None = None, cap: int | None = None,
+                       ws: torch.Tensor | None = None):
+    """Extremum-graph arcs (a, b) with their saddle vertices over a mesh
+    given as its symmetric CSR vertex adjacency: three int32 tensors."""
+    return _csr_pairs(label, row, col, order_field, sense, label_bound, cap, ws)
 
 
 class Batch:

@@ -80,11 +80,16 @@ __device__ __forceinline__ void append_global(const EmitArgs& a, unsigned long l
     }
 }
 
+// Key of the pair of labels c and m (both non-negative): (lo << shift) | hi.
+__device__ __forceinline__ unsigned long long pair_key_of(int shift, int32_t c, int32_t m) {
+    const uint32_t lo = (uint32_t)min(c, m), hi = (uint32_t)max(c, m);
+    return ((unsigned long long)lo << shift) | hi;
+}
+
 // Key of the pair of labels c and m, or kNoKey when m < 0.
 __device__ __forceinline__ unsigned long long pair_key(const EmitArgs& a, int32_t c, int32_t m) {
     if (m < 0) return kNoKey;
-    const uint32_t lo = (uint32_t)min(c, m), hi = (uint32_t)max(c, m);
-    return ((unsigned long long)lo << a.shift) | hi;
+    return pair_key_of(a.shift, c, m);
 }
 
 // Home slot of a key in the shared set: a multiplicative hash of both
@@ -530,17 +535,183 @@ int blocks_for(int64_t work, int per_sm) {
 
 bool adjacency_size_ok(int64_t n) { return n >= 0 && emit_capacity(n) <= (int64_t)INT32_MAX; }
 
-void size_adjacency_scratch(Sizer& s, int64_t n, bool saddle) {
-    const int64_t cap = emit_capacity(n);
-    s.take<int32_t>(64);
-    s.take<unsigned long long>(cap);
-    s.take<unsigned long long>(cap);
+namespace {
+
+// Workspace of one adjacency call: `cap` emitted keys (and crossing
+// vertices), the unique pass's chunk counts, the sort's scratch.
+struct PairScratch {
+    int32_t* ctl;
+    unsigned long long* k0;
+    unsigned long long* k1;
+    int32_t* w0;
+    int32_t* w1;
+    uint32_t* chunk;
+    SortScratch sort;
+    int64_t cap;
+};
+
+// The same sequence of pieces, sized (Sizer) and carved (Carver).
+void size_pair_scratch(Sizer& c, int64_t cap, bool saddle) {
+    c.take<int32_t>(64);
+    c.take<unsigned long long>(cap);
+    c.take<unsigned long long>(cap);
     if (saddle) {
-        s.take<int32_t>(cap);
-        s.take<int32_t>(cap);
+        c.take<int32_t>(cap);
+        c.take<int32_t>(cap);
     }
-    s.take<uint32_t>(ceil_div(cap, kChunk) + 1);
-    size_sort_scratch(s, cap);
+    c.take<uint32_t>(ceil_div(cap, kChunk) + 1);
+    size_sort_scratch(c, cap);
+}
+
+PairScratch take_pair_scratch(Carver& c, int64_t cap, bool saddle) {
+    PairScratch p;
+    p.cap = cap;
+    p.ctl = c.take<int32_t>(64);
+    p.k0 = c.take<unsigned long long>(cap);
+    p.k1 = c.take<unsigned long long>(cap);
+    p.w0 = saddle ? c.take<int32_t>(cap) : nullptr;
+    p.w1 = saddle ? c.take<int32_t>(cap) : nullptr;
+    p.chunk = c.take<uint32_t>(ceil_div(cap, kChunk) + 1);
+    p.sort = carve_sort_scratch(c, cap);
+    return p;
+}
+
+// Sort the emitted keys (with their crossing vertices), keep the first of
+// each run, and (saddles) reduce each run to its best crossing.
+int finish_pairs(const PairScratch& p, int shift, int32_t* out_a, int32_t* out_b, int64_t out_cap,
+                 int64_t* num_pairs, const int32_t* order, int sense, int32_t* saddle, int32_t* status,
+                 cudaStream_t s) {
+    const bool with_saddle = order != nullptr;
+    const int64_t cap = p.cap;
+    bool in_alt = false;
+    int r = run_sort_u64(p.k0, p.w0, p.k1, p.w1, p.ctl, cap, 2 * shift, p.sort, status, s, &in_alt,
+                         "adjacency.sort_hist", "adjacency.sort_pass");
+    if (r) return r;
+    const unsigned long long* sorted = in_alt ? p.k1 : p.k0;
+    const int32_t* cross = in_alt ? p.w1 : p.w0;
+    unsigned long long* best = in_alt ? p.k0 : p.k1;  // the other key buffer is free now
+    const int grid = blocks_for(ceil_div(cap, kChunk), 8);
+    {
+        TraceScope ts_("adjacency.heads", s);
+        k_adj_heads<<<grid, kThreads, 0, s>>>(sorted, p.ctl, cap, p.chunk);
+    }
+    MSC_LAUNCHED();
+    {
+        TraceScope ts_("adjacency.scan", s);
+        k_adj_scan<<<1, 1024, 0, s>>>(p.chunk, p.ctl, cap, num_pairs);
+    }
+    MSC_LAUNCHED();
+    if (with_saddle) {
+        {
+            TraceScope ts_("adjacency.zero", s);
+            k_adj_zero<<<blocks_for(ceil_div(cap, kThreads), 8), kThreads, 0, s>>>(best, num_pairs);
+        }
+        MSC_LAUNCHED();
+        {
+            TraceScope ts_("adjacency.write", s);
+            k_adj_write<true><<<grid, kThreads, 0, s>>>(sorted, p.ctl, cap, p.chunk, shift, out_a, out_b, out_cap,
+                                                        cross, order, sense, best);
+        }
+        MSC_LAUNCHED();
+        {
+            TraceScope ts_("adjacency.saddle", s);
+            k_adj_saddle<<<blocks_for(ceil_div(cap, kThreads), 8), kThreads, 0, s>>>(best, num_pairs, sense,
+                                                                                     saddle, out_cap);
+        }
+        MSC_LAUNCHED();
+    } else {
+        {
+            TraceScope ts_("adjacency.write", s);
+            k_adj_write<false><<<grid, kThreads, 0, s>>>(sorted, p.ctl, cap, p.chunk, shift, out_a, out_b, out_cap,
+                                                         nullptr, nullptr, 0, nullptr);
+        }
+        MSC_LAUNCHED();
+    }
+    return MSC_OK;
+}
+
+// Explicit mesh: one lane per vertex, the warp stepping through the rows of
+// its 32 vertices together (one entry per lane per step), each edge taken
+// from its smaller end.  A lane skips a key equal to the one it emitted
+// last (plain adjacency); the warp's keys of a step go out with one atomic.
+template <bool SADDLE>
+__global__ void __launch_bounds__(kThreads) k_adj_emit_csr(const int32_t* __restrict__ label,
+                                                           const int32_t* __restrict__ row,
+                                                           const int32_t* __restrict__ col, int32_t n, int64_t nnz,
+                                                           int32_t bound, int shift, const int32_t* __restrict__ order,
+                                                           int sense, unsigned long long* out, int32_t* out_w,
+                                                           int32_t* count, int64_t cap, int32_t* status) {
+    const int lane = threadIdx.x & 31;
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n; base += stride) {
+        const int64_t v = base + threadIdx.x;  // warp-uniform loop: every lane runs every step
+        int32_t l = -1, e0 = 0, e1 = 0, ov = 0;
+        if (v < n) {
+            l = __ldg(label + v);
+            if (l >= bound) {
+                record_error(status, MSC_ERR_ARG);
+                l = -1;
+            }
+            e0 = __ldg(row + v);
+            e1 = __ldg(row + v + 1);
+            if (e0 < 0 || e1 < e0 || (int64_t)e1 > nnz) {
+                record_error(status, MSC_ERR_ARG);
+                e1 = e0;
+            }
+            if (SADDLE && l >= 0) ov = __ldg(order + v);
+        }
+        const int32_t deg = l >= 0 ? e1 - e0 : 0;
+        int32_t steps = deg;
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) steps = max(steps, __shfl_xor_sync(0xffffffffu, steps, o));
+        unsigned long long last = kNoKey;
+        for (int32_t k = 0; k < steps; ++k) {
+            unsigned long long key = kNoKey;
+            int32_t w = 0;
+            if (k < deg) {
+                const int32_t u = __ldg(col + e0 + k);
+                if ((uint32_t)u >= (uint32_t)n) {
+                    record_error(status, MSC_ERR_ARG);
+                } else if (u > v) {
+                    const int32_t m = __ldg(label + u);
+                    if (m >= 0 && m < bound && m != l) {
+                        key = pair_key_of(shift, l, m);
+                        if constexpr (SADDLE) {
+                            const int32_t ou = __ldg(order + u);
+                            const bool u_is = sense > 0 ? ou < ov : ou > ov;
+                            w = u_is ? u : (int32_t)v;
+                        } else {
+                            if (key == last) key = kNoKey;  // the same pair as this lane's previous edge
+                            else last = key;
+                        }
+                    }
+                }
+            }
+            const uint32_t emit = __ballot_sync(0xffffffffu, key != kNoKey);
+            if (!emit) continue;
+            const int leader = __ffs(emit) - 1;
+            uint32_t pos0 = 0;
+            if (lane == leader) pos0 = atomicAdd(reinterpret_cast<uint32_t*>(count), (uint32_t)__popc(emit));
+            pos0 = __shfl_sync(0xffffffffu, pos0, leader);
+            if (key != kNoKey) {
+                const uint32_t pos = pos0 + __popc(emit & lanemask_lt());
+                if ((int64_t)pos < cap) {
+                    out[pos] = key;
+                    if constexpr (SADDLE) out_w[pos] = w;
+                } else {
+                    record_error(status, MSC_ERR_INTERNAL);  // more keys than entries: impossible
+                }
+            }
+        }
+    }
+}
+
+}  // namespace
+
+void size_adjacency_scratch(Sizer& s, int64_t n, bool saddle) { size_pair_scratch(s, emit_capacity(n), saddle); }
+
+void size_adjacency_csr_scratch(Sizer& s, int64_t nnz, bool saddle) {
+    size_pair_scratch(s, std::max<int64_t>(nnz, 1), saddle);
 }
 
 template <bool SADDLE>
@@ -564,67 +735,40 @@ int run_adjacency_grid(const int32_t* label, msc_grid g, int conn, int32_t bound
                        int32_t* status, cudaStream_t s, const int32_t* order, int sense, int32_t* saddle) {
     const bool with_saddle = order != nullptr;
     const int64_t n = (int64_t)g.nx * g.ny * g.nz;
-    const int64_t cap = emit_capacity(n);
     Carver c(ws, ws_bytes);
-    int32_t* ctl = c.take<int32_t>(64);
-    unsigned long long* k0 = c.take<unsigned long long>(cap);
-    unsigned long long* k1 = c.take<unsigned long long>(cap);
-    int32_t* w0 = with_saddle ? c.take<int32_t>(cap) : nullptr;
-    int32_t* w1 = with_saddle ? c.take<int32_t>(cap) : nullptr;
-    uint32_t* chunk = c.take<uint32_t>(ceil_div(cap, kChunk) + 1);
-    SortScratch sc = carve_sort_scratch(c, cap);
+    PairScratch p = take_pair_scratch(c, emit_capacity(n), with_saddle);
     if (!c.ok()) return MSC_ERR_WS;
-    MSC_TRY(cudaMemsetAsync(ctl, 0, 64 * sizeof(int32_t), s));
+    MSC_TRY(cudaMemsetAsync(p.ctl, 0, 64 * sizeof(int32_t), s));
     const int shift = ceil_log2(bound);
-    const EmitArgs ea{label, g.nx, g.ny, g.nz, bound, shift, k0, ctl, cap, status, order, sense, w0};
+    const EmitArgs ea{label, g.nx, g.ny, g.nz, bound, shift, p.k0, p.ctl, p.cap, status, order, sense, p.w0};
     const int64_t tiles = ceil_div(g.nx, kTX) * ceil_div(g.ny, kTY) * ceil_div(g.nz, kZR);
     int r = with_saddle ? launch_emit<true>(ea, conn, tiles, s) : launch_emit<false>(ea, conn, tiles, s);
     if (r) return r;
-    bool in_alt = false;
-    r = run_sort_u64(k0, w0, k1, w1, ctl, cap, 2 * shift, sc, status, s, &in_alt, "adjacency.sort_hist",
-                     "adjacency.sort_pass");
-    if (r) return r;
-    const unsigned long long* sorted = in_alt ? k1 : k0;
-    const int32_t* cross = in_alt ? w1 : w0;
-    unsigned long long* best = in_alt ? k0 : k1;  // the other key buffer is free now
-    const int grid = blocks_for(ceil_div(cap, kChunk), 8);
-    {
-        TraceScope ts_("adjacency.heads", s);
-        k_adj_heads<<<grid, kThreads, 0, s>>>(sorted, ctl, cap, chunk);
+    return finish_pairs(p, shift, out_a, out_b, out_cap, num_pairs, order, sense, saddle, status, s);
+}
+
+int run_adjacency_csr(const int32_t* label, const int32_t* row, const int32_t* col, int32_t n, int64_t nnz,
+                      int32_t bound, int32_t* out_a, int32_t* out_b, int64_t out_cap, int64_t* num_pairs, void* ws,
+                      size_t ws_bytes, int32_t* status, cudaStream_t s, const int32_t* order, int sense,
+                      int32_t* saddle) {
+    const bool with_saddle = order != nullptr;
+    Carver c(ws, ws_bytes);
+    PairScratch p = take_pair_scratch(c, std::max<int64_t>(nnz, 1), with_saddle);
+    if (!c.ok()) return MSC_ERR_WS;
+    MSC_TRY(cudaMemsetAsync(p.ctl, 0, 64 * sizeof(int32_t), s));
+    const int shift = ceil_log2(bound);
+    if (n > 0) {
+        TraceScope ts_("adjacency.emit_csr", s);
+        const int grid = blocks_for(ceil_div(n, kThreads), 8);
+        if (with_saddle)
+            k_adj_emit_csr<true><<<grid, kThreads, 0, s>>>(label, row, col, n, nnz, bound, shift, order, sense, p.k0,
+                                                           p.w0, p.ctl, p.cap, status);
+        else
+            k_adj_emit_csr<false><<<grid, kThreads, 0, s>>>(label, row, col, n, nnz, bound, shift, nullptr, 1, p.k0,
+                                                            nullptr, p.ctl, p.cap, status);
     }
     MSC_LAUNCHED();
-    {
-        TraceScope ts_("adjacency.scan", s);
-        k_adj_scan<<<1, 1024, 0, s>>>(chunk, ctl, cap, num_pairs);
-    }
-    MSC_LAUNCHED();
-    if (with_saddle) {
-        {
-            TraceScope ts_("adjacency.zero", s);
-            k_adj_zero<<<blocks_for(ceil_div(cap, kThreads), 8), kThreads, 0, s>>>(best, num_pairs);
-        }
-        MSC_LAUNCHED();
-        {
-            TraceScope ts_("adjacency.write", s);
-            k_adj_write<true><<<grid, kThreads, 0, s>>>(sorted, ctl, cap, chunk, shift, out_a, out_b, out_cap,
-                                                        cross, order, sense, best);
-        }
-        MSC_LAUNCHED();
-        {
-            TraceScope ts_("adjacency.saddle", s);
-            k_adj_saddle<<<blocks_for(ceil_div(cap, kThreads), 8), kThreads, 0, s>>>(best, num_pairs, sense,
-                                                                                     saddle, out_cap);
-        }
-        MSC_LAUNCHED();
-    } else {
-        {
-            TraceScope ts_("adjacency.write", s);
-            k_adj_write<false><<<grid, kThreads, 0, s>>>(sorted, ctl, cap, chunk, shift, out_a, out_b, out_cap,
-                                                         nullptr, nullptr, 0, nullptr);
-        }
-        MSC_LAUNCHED();
-    }
-    return MSC_OK;
+    return finish_pairs(p, shift, out_a, out_b, out_cap, num_pairs, order, sense, saddle, status, s);
 }
 
 }  // namespace msc

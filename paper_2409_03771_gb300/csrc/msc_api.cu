@@ -129,7 +129,6 @@ const char* msc_status_string(int code) {
 }
 
 size_t msc_workspace_bytes(int op, int64_t n, int64_t nnz) {
-    (void)nnz;
     if (n < 0 || n > INT32_MAX) return 0;
     Sizer s;
     switch (op) {
@@ -145,6 +144,11 @@ size_t msc_workspace_bytes(int op, int64_t n, int64_t nnz) {
         case MSC_OP_EXTREMUM_GRAPH:
             if (!adjacency_size_ok(n)) return 0;
             size_adjacency_scratch(s, n, op == MSC_OP_EXTREMUM_GRAPH);
+            return s.used;
+        case MSC_OP_ADJACENCY_CSR:
+        case MSC_OP_EXTREMUM_GRAPH_CSR:
+            if (nnz < 0 || nnz > INT32_MAX) return 0;
+            size_adjacency_csr_scratch(s, nnz, op == MSC_OP_EXTREMUM_GRAPH_CSR);
             return s.used;
         default: return 0;
     }
@@ -300,6 +304,33 @@ int msc_extremum_graph(const int32_t* label, const int32_t* order, msc_grid g, i
     MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
     return run_adjacency_grid(label, g, conn, label_bound, a, b, cap, num_arcs, ws, ws_bytes, d_status, s, order,
                               sense, saddle);
+}
+
+int msc_adjacency_csr(const int32_t* label, const int32_t* row, const int32_t* col, int32_t n, int64_t nnz,
+                      int32_t label_bound, int32_t* a, int32_t* b, int64_t cap, int64_t* num_pairs, void* ws,
+                      size_t ws_bytes, int32_t* d_status, void* stream) {
+    if (n < 0 || nnz < 0 || nnz > INT32_MAX || !num_pairs || !d_status || !ws || !ws_aligned(ws) ||
+        label_bound <= 0 || cap < 0 || (cap > 0 && (!a || !b)) || (n > 0 && (!label || !row || (nnz > 0 && !col))))
+        return MSC_ERR_ARG;
+    if (ws_bytes < msc_workspace_bytes(MSC_OP_ADJACENCY_CSR, n, nnz)) return MSC_ERR_WS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
+    return run_adjacency_csr(label, row, col, n, nnz, label_bound, a, b, cap, num_pairs, ws, ws_bytes, d_status, s);
+}
+
+int msc_extremum_graph_csr(const int32_t* label, const int32_t* order, const int32_t* row, const int32_t* col,
+                           int32_t n, int64_t nnz, int32_t label_bound, int32_t sense, int32_t* a, int32_t* b,
+                           int32_t* saddle, int64_t cap, int64_t* num_arcs, void* ws, size_t ws_bytes,
+                           int32_t* d_status, void* stream) {
+    if (n < 0 || nnz < 0 || nnz > INT32_MAX || !num_arcs || !d_status || !ws || !ws_aligned(ws) ||
+        label_bound <= 0 || (sense != 1 && sense != -1) || cap < 0 || (cap > 0 && (!a || !b || !saddle)) ||
+        (n > 0 && (!label || !order || !row || (nnz > 0 && !col))))
+        return MSC_ERR_ARG;
+    if (ws_bytes < msc_workspace_bytes(MSC_OP_EXTREMUM_GRAPH_CSR, n, nnz)) return MSC_ERR_WS;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    MSC_TRY(cudaMemsetAsync(d_status, 0, sizeof(int32_t), s));
+    return run_adjacency_csr(label, row, col, n, nnz, label_bound, a, b, cap, num_arcs, ws, ws_bytes, d_status, s,
+                             order, sense, saddle);
 }
 
 }  // extern "C"

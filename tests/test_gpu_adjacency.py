@@ -308,3 +308,111 @@ def test_graph_full_size_512(m):
             torch.cuda.empty_cache()
         del order, asc, desc
         torch.cuda.empty_cache()
+
+
+# ---------------------------------------------------------------------------
+# explicit meshes (msc_adjacency_csr, msc_extremum_graph_csr)
+
+
+def random_csr(n, m, rng):
+    edges = {(int(min(a, b)), int(max(a, b))) for a, b in rng.integers(0, n, (m, 2)) if a != b}
+    adj = [[] for _ in range(n)]
+    for u, v in edges:
+        adj[u].append(v)
+        adj[v].append(u)
+    row = np.zeros(n + 1, np.int32)
+    for v in range(n):
+        row[v + 1] = row[v] + len(adj[v])
+    col = np.array([u for v in range(n) for u in sorted(adj[v])], np.int32)
+    return row, col
+
+
+def check_csr(m, oracle_mod, lab, row, col, order=None, sense=1, bound=None):
+    lab = np.ascontiguousarray(lab, np.int32)
+    want = oracle_mod.adjacency_csr(lab, row, col, order, sense)
+    t = lambda x: torch.as_tensor(np.ascontiguousarray(x, np.int32)).cuda()
+    if order is None:
+        got = m.adjacency_csr(t(lab), t(row), t(col), label_bound=bound)
+    else:
+        got = m.extremum_graph_csr(t(lab), t(order), t(row), t(col), sense, label_bound=bound)
+    assert len(got) == len(want)
+    for x, y in zip(got, want):
+        np.testing.assert_array_equal(x.cpu().numpy(), y)
+    return want[0].size
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_mesh_random_graphs(m, oracle_mod, seed):
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(1000, 40000))
+    row, col = random_csr(n, 4 * n, rng)
+    lab = rng.integers(-1, 60, n).astype(np.int32)
+    order = rng.permutation(n).astype(np.int32)
+    assert check_csr(m, oracle_mod, lab, row, col, bound=60) > 100
+    for sense in (1, -1):
+        check_csr(m, oracle_mod, lab, row, col, order, sense, bound=60)
+
+
+def test_mesh_segmentation_labels(m, oracle_mod):
+    """A thinned, permuted Kuhn mesh segmented by the oracle: maxima and
+    minima arcs with saddles, and cell adjacency."""
+    row, col = workloads.tet_mesh_csr(edge=24, delete_frac=0.4, seed=5)
+    row, col = row.numpy(), col.numpy()
+    n = row.size - 1
+    f = np.random.default_rng(6).random(n, dtype=np.float32)
+    order = oracle_mod.order(f)
+    asc_ptr, desc_ptr = oracle_mod.steepest_csr(order, row, col)
+    asc, desc = oracle_mod.walk(asc_ptr), oracle_mod.walk(desc_ptr)
+    ms, cells = oracle_mod.ms(asc, desc)
+    assert check_csr(m, oracle_mod, desc, row, col, order, 1) > 10
+    assert check_csr(m, oracle_mod, asc, row, col, order, -1) > 10
+    assert check_csr(m, oracle_mod, ms, row, col, bound=cells) > 10
+
+
+def test_mesh_edge_cases(m, oracle_mod):
+    rng = np.random.default_rng(4)
+    # no edges at all, a single vertex, isolated vertices among edges
+    for n, mm in ((50, 0), (1, 0), (300, 40)):
+        row, col = random_csr(n, mm, rng)
+        lab = rng.integers(0, 5, n).astype(np.int32)
+        check_csr(m, oracle_mod, lab, row, col, bound=5)
+        check_csr(m, oracle_mod, lab, row, col, rng.permutation(n).astype(np.int32), 1, bound=5)
+    # a column out of range is an argument error
+    row = torch.tensor([0, 1, 2], dtype=torch.int32, device="cuda")
+    col = torch.tensor([1, 7], dtype=torch.int32, device="cuda")
+    with pytest.raises(m.MSCError) as e:
+        m.adjacency_csr(torch.zeros(2, dtype=torch.int32, device="cuda"), row, col)
+    assert e.value.code == m.ERR_ARG
+
+
+def test_mesh_full_size_256(m):
+    """The benchmarked mesh (256^3 Kuhn split, 40 % of tetrahedra deleted,
+    ids permuted; 16.7M vertices): maxima arcs and saddles of a random field
+    equal a plain PyTorch group-by over every CSR entry."""
+    row, col = workloads.tet_mesh_csr(edge=256, delete_frac=0.4, seed=3, device="cuda")
+    n = row.numel() - 1
+    g = torch.Generator(device="cuda").manual_seed(11)
+    f = torch.rand(n, device="cuda", generator=g)
+    order = m.order(f)
+    asc_ptr, desc_ptr = m.steepest_csr(order, row, col)
+    desc = m.compress(desc_ptr)
+    a, b, s = m.extremum_graph_csr(desc, order, row, col, 1)
+    deg = (row[1:] - row[:-1]).long()
+    src = torch.repeat_interleave(torch.arange(n, device="cuda"), deg)
+    dst = col.long()
+    keep = dst > src
+    src, dst = src[keep], dst[keep]
+    la, lb = desc.long()[src], desc.long()[dst]
+    on = la != lb
+    src, dst, la, lb = src[on], dst[on], la[on], lb[on]
+    shift = max(int(n - 1).bit_length(), 0)
+    keys = (torch.minimum(la, lb) << shift) | torch.maximum(la, lb)
+    o = order.long()
+    w = torch.where(o[src] < o[dst], src, dst)
+    vals = (o[w] << 32) | w
+    uk, inv = torch.unique(keys, return_inverse=True)
+    best = torch.full((uk.numel(),), -1, dtype=torch.int64, device="cuda")
+    best.scatter_reduce_(0, inv, vals, reduce="amax")
+    assert a.numel() == uk.numel()
+    assert torch.equal((a.long() << shift) | b.long(), uk)
+    assert torch.equal(s.long(), best & 0xFFFFFFFF)

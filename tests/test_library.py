@@ -93,6 +93,15 @@ def test_host_argument_checks_need_no_gpu(lib):
     assert m.msc_extremum_graph(16, 16, (4, 4, 4), 14, 64, 0, **gargs) == m.ERR_ARG
     assert m.msc_extremum_graph(16, 16, (4, 4, 4), 14, 64, 1, **dict(gargs, saddle=0)) == m.ERR_ARG
     assert m.msc_extremum_graph(16, 16, (4, 4, 4), 14, 64, -1, **dict(gargs, ws_bytes=ws)) == m.ERR_WS
+    # mesh variants: sizes, bounds, workspace
+    cws = m.msc_workspace_bytes(m.OP_ADJACENCY_CSR, 100, 1000)
+    assert m.msc_workspace_bytes(m.OP_EXTREMUM_GRAPH_CSR, 100, 1000) > cws > 1000 * 16
+    assert m.msc_workspace_bytes(m.OP_ADJACENCY_CSR, 100, 2 ** 31) == 0
+    assert m.msc_adjacency_csr(16, 16, 16, 100, 1000, 0, 16, 16, 4, 16, 256, cws, 16, stream=0) == m.ERR_ARG
+    assert m.msc_adjacency_csr(16, 16, 16, 100, -1, 100, 16, 16, 4, 16, 256, cws, 16, stream=0) == m.ERR_ARG
+    assert m.msc_adjacency_csr(16, 16, 16, 100, 1000, 100, 16, 16, 4, 16, 256, cws - 1, 16, stream=0) == m.ERR_WS
+    assert m.msc_extremum_graph_csr(16, 0, 16, 16, 100, 1000, 100, 1, 16, 16, 16, 4, 16, 256, cws, 16,
+                                    stream=0) == m.ERR_ARG
 
 
 def test_no_cpu_fallback():
