@@ -454,6 +454,7 @@ def run_ours(args):
             # the extremum graph: maxima / minima arcs with their saddles
             ("smooth", "desc", seg_out[0][2], n, seg_out[0][0], 1), ("smooth", "asc", seg_out[0][1], n, seg_out[0][0], -1),
             ("noise", "desc", seg_out[1][2], n, seg_out[1][0], 1)])
+        out["adjacency"]["mesh"] = mesh_graph_bench(dev, row, col)
     if not args.no_batch:
         del f_smooth, f_noise, mask, row, col, seg_out, lab, mlab, ws
         torch.cuda.empty_cache()
@@ -700,6 +701,49 @@ def adjacency_bench(dev, dims, cases, reps=3):
     return {"workload": (f"adjacency of the step's {dims[0]}^3 maximum labels and cell ids, and the extremum graph "
                          f"(arcs + saddles) of its maximum and minimum labels; 14-neighbour link"),
             "rows": rows}
+
+
+def mesh_graph_bench(dev, row, col, reps=3):
+    """Extremum graph over the step's explicit mesh: maxima of a seeded
+    uniform field on its vertices (order, steepest pointers over the CSR and
+    pointer jumping by the library), arcs and saddles over its edges."""
+    import torch
+
+    import paper_2409_03771_gb300 as msc
+
+    n, nnz = row.numel() - 1, col.numel()
+    g = torch.Generator(device=dev).manual_seed(11)
+    f = torch.rand(n, device=dev, generator=g)
+    order = msc.order(f)
+    _, desc_ptr = msc.steepest_csr(order, row, col)
+    desc = msc.compress(desc_ptr)
+    del f, desc_ptr
+    ws = torch.empty(msc.msc_workspace_bytes(msc.OP_EXTREMUM_GRAPH_CSR, n, nnz), dtype=torch.uint8, device=dev)
+    st = torch.zeros(1, dtype=torch.int32, device=dev)
+    k = torch.zeros(1, dtype=torch.int64, device=dev)
+    cap = max(nnz, 1)
+    a, b, sad = (torch.empty(cap, dtype=torch.int32, device=dev) for _ in range(3))
+    stream = torch.cuda.current_stream(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+    def run():
+        r = msc.msc_extremum_graph_csr(desc, order, row, col, n, nnz, n, 1, a, b, sad, cap, k, ws, ws.numel(), st,
+                                       stream)
+        assert r == 0, msc.msc_status_string(r)
+
+    run()
+    torch.cuda.synchronize()
+    ev0.record(stream)
+    for _ in range(reps):
+        run()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    if int(st.item()) != 0:
+        raise RuntimeError(f"mesh extremum graph: device status {int(st.item())}")
+    ms = ev0.elapsed_time(ev1) / reps
+    return {"workload": f"extremum graph (maxima, saddles) of a uniform field on the step's mesh ({n} vertices, "
+                        f"{nnz} CSR entries)", "arcs": int(k.item()), "ms": round(ms, 3),
+            "vertices_per_s": n / (ms / 1e3)}
 
 
 # ---------------------------------------------------------------------------
