@@ -141,15 +141,19 @@ class ClockSampler:
 
 
 def sources_sha(names):
-    """Hash of the kernel source files `names` (in the package's csrc) and the
-    headers every kernel includes."""
+    """Hash of the kernel source files `names` (in the package's csrc), their
+    own headers and the device helpers every kernel includes (the public
+    header only declares entry points and is left out)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2409_03771_gb300", "csrc")
-    for f in ["common.cuh", "tma.cuh"] + sorted(names):
+    files = ["common.cuh", "tma.cuh"]
+    for f in sorted(names):
+        files.append(f)
+        if os.path.exists(os.path.join(csrc, f[:-3] + ".cuh")):
+            files.append(f[:-3] + ".cuh")
+    for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())
-    with open(os.path.join(ROOT, "include", "msc.h"), "rb") as fh:
-        h.update(fh.read())
     return h.hexdigest()[:16]
 
 
