@@ -4,9 +4,10 @@
 // lexicographic order, minimum first.
 //
 // 1. A linear-probing hash table de-duplicates the pair keys
-//    asc * n + desc.  Its capacity is a power of two >= 2 * min(n,
-//    #minima * #maxima), chosen on the device, so smooth fields (few
-//    extrema) use a table that lives in L2.  Within a warp, a run of
+//    asc * n + desc.  Its capacity is a power of two >= 2 * #minima *
+//    #maxima, or >= n when that is more than n (there are at most n
+//    distinct pairs), chosen on the device, so smooth fields (few extrema)
+//    use a table that lives in L2.  Within a warp, a run of
 //    consecutive vertices with the same key (neighbours usually share a
 //    cell) probes once.
 //    Each vertex keeps its slot in `ms` for now.
@@ -67,8 +68,12 @@ __global__ void k_ms_prepare(const int32_t* __restrict__ asc, const int32_t* __r
 __global__ void k_ms_setcap(uint32_t* ctl, int64_t n, int64_t cap_max) {
     const unsigned long long pairs = (unsigned long long)ctl[0] * ctl[1];
     const unsigned long long bound = pairs < (unsigned long long)n ? pairs : (unsigned long long)n;
+    // twice the bound on the distinct pairs while that stays within n, else
+    // the bound itself (there are at most n pairs; white noise fills a
+    // table of n slots to about a third)
+    const unsigned long long want = 2 * bound <= (unsigned long long)n ? 2 * bound : bound;
     unsigned long long cap = 64;
-    while (cap < 2 * bound) cap <<= 1;
+    while (cap < want) cap <<= 1;
     if ((long long)cap > cap_max) cap = (unsigned long long)cap_max;
     ctl[2] = (uint32_t)cap;  // cap_max <= 2^31
     ctl[3] = 0;
