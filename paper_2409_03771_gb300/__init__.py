@@ -553,8 +553,9 @@ def _csr_pairs(label, row, col, order, sense, label_bound, cap, ws):
             code = msc_adjacency_csr(lab, row, col, n, nnz, bound, a, b, cap, k, ws, ws.numel(), st)
         else:
             code = msc_extremum_graph_csr(lab, o, row, col, n, nnz, bound, sense, a, b, s, cap, k, ws, ws.numel(), st)
-        _check(code, "msc_adjacency_csr")
-        _finish(st, "msc_adjacency_csr")
+        where = "msc_adjacency_csr" if o is None else "msc_extremum_graph_csr"
+        _check(code, where)
+        _finish(st, where)
         K = int(k.item())
         if K <= cap:
             return (a[:K], b[:K]) if o is None else (a[:K], b[:K], s[:K])
