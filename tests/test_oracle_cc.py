@@ -200,3 +200,43 @@ def test_alg3_fixed_point_partition_equals_bfs(oracle_mod, seed):
         if lab[v] >= 0:
             comp = np.nonzero(lab == lab[v])[0]
             assert d[v] == comp.max() and lab[v] == comp.min()
+
+
+def test_mesh_components_match_networkx(oracle_mod):
+    """The components of a thinned Kuhn mesh equal networkx's connected
+    components (a library routine), with the smallest id as the label."""
+    nx_ = pytest.importorskip("networkx")
+    row, col = workloads.tet_mesh_csr(edge=10, delete_frac=0.5, seed=21)
+    row, col = row.numpy(), col.numpy()
+    n = row.size - 1
+    g = nx_.Graph()
+    g.add_nodes_from(range(n))
+    for v in range(n):
+        g.add_edges_from((v, int(u)) for u in col[row[v]:row[v + 1]])
+    want = np.empty(n, np.int32)
+    for comp in nx_.connected_components(g):
+        want[list(comp)] = min(comp)
+    np.testing.assert_array_equal(oracle_mod.cc_csr(row, col), want)
+
+
+@pytest.mark.parametrize("conn", [6, 14])
+def test_grid_components_match_networkx(oracle_mod, conn):
+    nx_ = pytest.importorskip("networkx")
+    dims = (9, 7, 5)
+    rng = np.random.default_rng(conn)
+    mask = (rng.random(9 * 7 * 5) < 0.45).astype(np.uint8)
+    offs = [(1, 0, 0), (0, 1, 0), (0, 0, 1)] + ([(1, 1, 0), (1, 0, 1), (0, 1, 1), (1, 1, 1)] if conn == 14 else [])
+    g = nx_.Graph()
+    ids = [v for v in range(mask.size) if mask[v]]
+    g.add_nodes_from(ids)
+    for v in ids:
+        x, y, z = v % 9, (v // 9) % 7, v // 63
+        for dx, dy, dz in offs:
+            if x + dx < 9 and y + dy < 7 and z + dz < 5:
+                u = (x + dx) + 9 * ((y + dy) + 7 * (z + dz))
+                if mask[u]:
+                    g.add_edge(v, u)
+    want = np.full(mask.size, -1, np.int32)
+    for comp in nx_.connected_components(g):
+        want[list(comp)] = min(comp)
+    np.testing.assert_array_equal(oracle_mod.cc_grid(mask, dims, conn), want)
