@@ -200,3 +200,18 @@ def test_sampled_helpers_match_full_arrays(oracle_mod):
     for v in np.random.default_rng(0).integers(0, f.size, 60):
         assert oracle_mod.steepest_at(f, dims, int(v)) == (asc_ptr[v], desc_ptr[v])
         assert oracle_mod.labels_at(f, dims, int(v)) == (asc[v], desc[v])
+
+
+def test_order_matches_numpy_lexsort(oracle_mod):
+    """At a size counting cannot reach: the rank under (f, id) from numpy's
+    stable lexsort (a library routine), with heavy ties and signed zeros."""
+    rng = np.random.default_rng(44)
+    n = 200_003
+    f = (rng.integers(-300, 300, n) / 8.0).astype(np.float32)
+    f[::11] = -0.0
+    f[5::13] = np.inf
+    f[7::17] = -np.inf
+    perm = np.lexsort((np.arange(n), f))  # sorted ids: by f, ties by id (-0.0 == +0.0)
+    want = np.empty(n, np.int32)
+    want[perm] = np.arange(n, dtype=np.int32)
+    np.testing.assert_array_equal(oracle_mod.order(f), want)
