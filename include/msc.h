@@ -132,14 +132,17 @@ MSC_API int msc_compress(int32_t* ptr, int32_t n, void* ws, size_t ws_bytes, int
                  void* stream);
 
 /* Path compression for callers that cannot allocate device memory.  The
- * paper has no counterpart: this entry point exists for code that must not
- * call cudaMalloc -- a host function enqueued on a stream (such callbacks
- * may not make CUDA calls), a process whose device memory is owned by
- * another allocator or a fixed budget (a serving runtime, a plugin inside a
- * framework), or code that must not risk the device-wide synchronisation
- * that allocating and freeing can cause.  It does what msc_compress does,
- * with the same arguments minus the workspace, and allocates nothing (no
- * cudaMalloc, cudaFree or allocating library routine).
+ * paper has no counterpart.  Some callers must not call cudaMalloc: a
+ * process whose device memory belongs to another allocator or to a fixed
+ * budget (a serving runtime, a plugin inside a framework that owns the
+ * device), or code that must not risk the device-wide synchronisation that
+ * allocating and freeing can cause.  This entry point does what
+ * msc_compress does, with the same arguments minus the workspace, and
+ * allocates nothing (no cudaMalloc, cudaFree or allocating library
+ * routine).  It is an ordinary host call that enqueues work on `stream`
+ * (a memset, an occupancy query and about log4(n) + 3 kernel launches), so
+ * it must not be made from a host function enqueued on a stream, where CUDA
+ * calls are not allowed.
  *   n  at most MSC_NOALLOC_MAX_N; larger n returns MSC_ERR_TOO_LARGE.
  * Scratch: a static device array of about 2 MiB (step counters and two
  * active lists of MSC_NOALLOC_MAX_N / 16 + 1 entries), which every GPU that
@@ -147,9 +150,13 @@ MSC_API int msc_compress(int32_t* ptr, int32_t n, void* ws, size_t ws_bytes, int
  * keeps the last call's contents (the counters are cleared on every call):
  * calls that overlap on the GPU -- on different streams, or on different
  * host threads without ordering -- race on it and must not be issued.
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress with that device current); make that first call
- * before any stream capture. */
+ * First call on a device: it looks up the array's device address
+ * (cudaGetSymbolAddress with that device current), and with lazy module
+ * loading (the CUDA default) that lookup and the first launches may load
+ * the library's device code, which places the static array in device
+ * memory -- a driver-side allocation that can synchronise.  So make one
+ * warm-up call on each device (any n >= 1) before entering the context
+ * that must not allocate, and before any stream capture. */
 #define MSC_NOALLOC_MAX_N (1 << 22)
 MSC_API int msc_compress_noalloc(int32_t* ptr, int32_t n, int32_t* d_status, void* stream);
 

@@ -34,6 +34,7 @@ struct JumpArray {
     JumpCtl* ctl;
     int32_t* list0;
     int32_t* list1;
+    int64_t list_cap;  // entries of list0 and of list1
 };
 
 struct JumpPair {
@@ -186,7 +187,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, 
 #pragma unroll
             for (int j = 0; j < kPerThread; ++j)
                 if (ch & (1u << j)) {
-                    MSC_GUARD(off < (uint32_t)n / 2 + 1, status, -122)
+                    MSC_GUARD((int64_t)off < A.list_cap, status, -122)
                     out_list[off] = vid[j];
                     ++off;
                 }
@@ -247,6 +248,7 @@ int run_compress(int32_t* const* ptrs, int count, int32_t n, const CompressScrat
         pr.a[i].ctl = sc.ctl + i;
         pr.a[i].list0 = sc.lists + (size_t)i * 2 * sc.list_cap;
         pr.a[i].list1 = pr.a[i].list0 + sc.list_cap;
+        pr.a[i].list_cap = sc.list_cap;
     }
     const int build_shift = std::max(1, std::min(tune.build_shift, 30));
     auto kern = tune.trusted ? k_jump<false> : k_jump<true>;

@@ -1,12 +1,14 @@
 """msc_compress_noalloc: path compression for callers that cannot allocate
-device memory (host functions enqueued on a stream, processes whose device
-memory belongs to another allocator or a fixed budget, code that must not
-risk the synchronisation allocation can cause).  It keeps its scratch in a
-static device array instead of a caller workspace.
+device memory (processes whose device memory belongs to another allocator or
+a fixed budget, code that must not risk the synchronisation allocation can
+cause).  It keeps its scratch in a static device array instead of a caller
+workspace.
 
 Checked through the C ABI against msc_compress (the workspace entry point),
 bit for bit, on two calls in a row with different sizes and data -- the
-second call must not see anything the first left in the shared array.
+second call must not see anything the first left in the shared array -- and
+against the oracle's memoised walk to each vertex's root.  A call at the
+maximum size leaves the device's free memory unchanged.
 This file is collected last so that a run stopping at the first failure has
 run every other test first; it also passes alone in a fresh process.
 """
@@ -54,15 +56,28 @@ def run_both(m, ptr_host):
     return ref, got
 
 
-def test_noalloc_matches_workspace_entry_on_two_calls_in_a_row(m):
+def test_noalloc_matches_workspace_entry_on_two_calls_in_a_row(m, oracle_mod):
     first = chains(m.NOALLOC_MAX_N, seed=1, roots=3, span=2)  # maximum size, long paths
     second = chains(1_000_003, seed=2, roots=50, span=7)  # smaller, different data
     for host in (first, second):
         ref, got = run_both(m, host)
         assert torch.equal(ref, got)
-    # the result is the true root of every vertex, not just equal to msc_compress
-    roots = got.cpu().numpy()
-    assert (second[roots] == roots).all()
+        # every entry is its vertex's root, as the oracle's walk finds it
+        np.testing.assert_array_equal(got.cpu().numpy(), oracle_mod.walk_memo(host))
+
+
+def test_noalloc_leaves_free_device_memory_unchanged(m):
+    host = chains(m.NOALLOC_MAX_N, seed=3, roots=5, span=3)
+    ptr = torch.from_numpy(host).cuda()
+    warm = torch.zeros(1, dtype=torch.int32, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert m.msc_compress_noalloc(warm, 1, st) == m.OK  # warm-up: loads the device code
+    torch.cuda.synchronize()
+    free_before = torch.cuda.mem_get_info()[0]
+    assert m.msc_compress_noalloc(ptr, ptr.numel(), st) == m.OK
+    torch.cuda.synchronize()
+    assert int(st.item()) == m.OK
+    assert torch.cuda.mem_get_info()[0] == free_before
 
 
 def test_noalloc_rejects_sizes_beyond_its_scratch(m):
