@@ -18,7 +18,7 @@ INCLUDE = os.path.join(ROOT, "include")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "libmsc.so")
 
-SOURCES = ["sort.cu", "steepest.cu", "compress.cu", "msid.cu", "cc.cu", "msc_api.cu", "trace.cu", "batch.cu",
+SOURCES = ["sort.cu", "order.cu", "steepest.cu", "compress.cu", "msid.cu", "cc.cu", "msc_api.cu", "trace.cu", "batch.cu",
            "serve.cu", "adjacency.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "-Xcompiler", "-fvisibility=hidden"]

@@ -456,7 +456,9 @@ int msc_batch_plan_create(const msc_grid* grids, int32_t count, const float* f, 
     p->T = resolve(grids, count, tune);
     p->d = carve_all(ws, ws_bytes, p->L);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
-    if ((r = upload_tables(ws, p->L, p->d, s)) || (cudaStreamSynchronize(s) != cudaSuccess && (r = MSC_ERR_CUDA))) {
+    r = upload_tables(ws, p->L, p->d, s);
+    if (!r && cudaStreamSynchronize(s) != cudaSuccess) r = MSC_ERR_CUDA;
+    if (r) {
         delete p;
         return r;
     }

@@ -1,10 +1,13 @@
-// Onesweep LSD radix sort for the vertex order (Simulation of Simplicity,
-// section "Preprocessing": sort by value, ties by global id).
+// Onesweep LSD radix sorts: the vertex order of many packed instances at
+// once (Simulation of Simplicity, section "Preprocessing": sort by value,
+// ties by global id, per instance) and 64-bit keys with an int32 payload
+// (unique Morse-Smale pairs, region-adjacency keys); plus the inversion of
+// the vertex order that order.cu shares.
 //
-// Keys: float32 bits mapped to an order-preserving uint32 (-0.0 first
-// folded onto +0.0 so that the two tie, as IEEE '<' says).  Four 8-bit
-// digit passes, least significant first; every pass is stable, and the
-// first pass reads the vertices in id order, so equal keys stay in id
+// Keys of a float field: float32 bits mapped to an order-preserving uint32
+// (-0.0 first folded onto +0.0 so that the two tie, as IEEE '<' says).
+// 8-bit digit passes, least significant first; every pass is stable, and
+// the first pass reads the vertices in id order, so equal keys stay in id
 // order: the final position of v is its rank under (f[v], v).
 //
 // One pass = one kernel.  A block takes tiles of 4096 keys from a global
@@ -12,8 +15,8 @@
 // ranks its keys per digit stably within each warp (ballot peers +
 // per-warp counters), publishes its per-digit counts to a decoupled
 // look-back array, sums its predecessors' counts and scatters through
-// shared memory.  The last pass files (vertex id, position) pairs into
-// buckets of consecutive ids; the order field is their inverse
+// shared memory.  The last pass of an order files (vertex id, position)
+// pairs into buckets of consecutive ids; the order field is their inverse
 // permutation, written through shared memory: the buckets are split into
 // sub-buckets of 2^15 ids, each scattered into one CTA's shared memory and
 // written out as whole lines (k_pair_split, k_pair_scatter_local).
@@ -22,6 +25,7 @@
 #include <algorithm>
 #include <utility>
 
+#include "radix.cuh"
 #include "sort.cuh"
 
 namespace msc {
@@ -41,111 +45,10 @@ constexpr uint32_t kSpinLimit = 1u << 22;
 // buckets of 2^shift consecutive ids; bucket b holds exactly the ids
 // [b << shift, (b + 1) << shift) and so occupies pair slots of the same
 // range.  At most kMaxBuckets buckets (see bucket_shift).
-constexpr int kMaxBuckets = 256;
-constexpr int kFillStride = 32;  // one 128-byte line per bucket counter: the
+constexpr int kMaxBuckets = kOrderMaxBuckets;
+constexpr int kFillStride = kOrderFillStride;  // one 128-byte line per bucket counter: the
                                  // tiles' reservations spread over L2 slices
 constexpr int kCounterWords = 8 + kMaxBuckets * kFillStride;  // tile counters, bucket fills
-
-__device__ __forceinline__ uint32_t float_key(float x) {
-    uint32_t u = __float_as_uint(x);
-    if (u == 0x80000000u) u = 0u;  // -0.0 ties with +0.0
-    return (u & 0x80000000u) ? ~u : (u | 0x80000000u);
-}
-
-__device__ __forceinline__ bool is_nan_bits(float x) {
-    return (__float_as_uint(x) & 0x7fffffffu) > 0x7f800000u;
-}
-
-// Inclusive scan over 256 values held one per thread (kThreads == 256).
-__device__ __forceinline__ uint32_t block_scan_256(uint32_t v, uint32_t* s_w) {
-    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-#pragma unroll
-    for (int o = 1; o < 32; o <<= 1) {
-        const uint32_t t = __shfl_up_sync(0xffffffffu, v, o);
-        if (lane >= o) v += t;
-    }
-    if (lane == 31) s_w[warp] = v;
-    __syncthreads();
-    if (warp == 0) {
-        uint32_t t = lane < kWarps ? s_w[lane] : 0u;
-#pragma unroll
-        for (int o = 1; o < kWarps; o <<= 1) {
-            const uint32_t q = __shfl_up_sync(0xffffffffu, t, o);
-            if (lane >= o) t += q;
-        }
-        if (lane < kWarps) s_w[lane] = t;
-    }
-    __syncthreads();
-    if (warp > 0) v += s_w[warp - 1];
-    __syncthreads();
-    return v;
-}
-
-// Lanes of the warp whose 8-bit digit equals this lane's (valid lanes
-// only), from eight ballots -- no match instruction, no divergence.
-__device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
-    uint32_t eq = __ballot_sync(0xffffffffu, valid);
-#pragma unroll
-    for (int b = 0; b < 8; ++b) {
-        const bool bit = (d >> b) & 1u;
-        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
-        eq &= bit ? bal : ~bal;
-    }
-    return eq;
-}
-
-constexpr int kHistRun = 16;  // consecutive keys per thread in the histogram
-
-// Digit histograms for `npass` passes over n keys (keys read from `keys`,
-// or made from the float field `f`).  Each thread counts runs of equal
-// digits over 16 consecutive keys (neighbouring grid values share their
-// high digits, so the skewed digits cost one update per run) into a
-// warp-private shared histogram; blocks then add theirs to the global one.
-// Loads the float keys f[i0 .. i0+cnt) (cnt <= 16; the rest become 0)
-// into k[], noting NaNs.
-__device__ __forceinline__ void load_float_keys16(const float* __restrict__ f, int64_t i0, int cnt,
-                                                  uint32_t (&k)[kHistRun], bool& saw_nan) {
-    if (cnt == kHistRun && ((uintptr_t)(f + i0) & 15) == 0) {
-#pragma unroll
-        for (int q = 0; q < kHistRun / 4; ++q) {
-            const float4 v = reinterpret_cast<const float4*>(f + i0)[q];
-            saw_nan |= is_nan_bits(v.x) | is_nan_bits(v.y) | is_nan_bits(v.z) | is_nan_bits(v.w);
-            k[4 * q + 0] = float_key(v.x);
-            k[4 * q + 1] = float_key(v.y);
-            k[4 * q + 2] = float_key(v.z);
-            k[4 * q + 3] = float_key(v.w);
-        }
-    } else {
-#pragma unroll
-        for (int j = 0; j < kHistRun; ++j) {
-            const float x = j < cnt ? f[i0 + j] : 0.f;
-            saw_nan |= j < cnt && is_nan_bits(x);
-            k[j] = float_key(x);
-        }
-    }
-}
-
-// Adds the digits of k[0 .. cnt) for `npass` passes to the histograms h
-// ([npass][256]), one shared atomic per run of equal digits.
-template <typename KeyT>
-__device__ __forceinline__ void count_runs(const KeyT (&k)[kHistRun], int cnt, int npass, uint32_t* h) {
-    for (int p = 0; p < npass; ++p, h += kBins) {
-        uint32_t cur = (uint32_t)(k[0] >> (8 * p)) & 255u, run = 1;
-#pragma unroll
-        for (int j = 1; j < kHistRun; ++j) {
-            if (j >= cnt) break;
-            const uint32_t d = (uint32_t)(k[j] >> (8 * p)) & 255u;
-            if (d == cur) {
-                ++run;
-            } else {
-                atomicAdd(&h[cur], run);
-                cur = d;
-                run = 1;
-            }
-        }
-        atomicAdd(&h[cur], run);
-    }
-}
 
 // Digit histograms for `npass` passes over n keys (keys read from `keys`,
 // or made from the float field `f`).  Each thread counts runs of equal
@@ -681,7 +584,15 @@ int launch_pass(const PassArgs<KeyT>& a, int64_t max_n, cudaStream_t s, const ch
 
 }  // namespace
 
+int order_bucket_shift(int64_t n) { return bucket_shift(n); }
+
+int order_invert(int shift, const int32_t* ids, const uint32_t* pos, int32_t* ids2, uint32_t* pos2,
+                 uint32_t* sub_fill, int64_t n, int32_t* order, int32_t* status, cudaStream_t s) {
+    return launch_pair_split_scatter(shift, ids, pos, ids2, pos2, sub_fill, n, order, status, s);
+}
+
 void size_sort_scratch(Sizer& s, int64_t n) {
+    s.take<uint32_t>(kOrderCntWords);
     s.take<uint32_t>(8 * kBins + kCounterWords);
     s.take<uint32_t>(ceil_div(std::max<int64_t>(n, 1), kSubIds) + 1);
     s.take<unsigned long long>((size_t)std::max<int64_t>(1, ceil_div(n, kSortTile)) * kBins);
@@ -689,19 +600,13 @@ void size_sort_scratch(Sizer& s, int64_t n) {
 
 SortScratch carve_sort_scratch(Carver& c, int64_t n) {
     SortScratch sc;
+    sc.ord_cnt = c.take<uint32_t>(kOrderCntWords);
     sc.hist = c.take<uint32_t>(8 * kBins + kCounterWords);
     sc.tile_counters = sc.hist + 8 * kBins;
     sc.sub_fill = c.take<uint32_t>(ceil_div(std::max<int64_t>(n, 1), kSubIds) + 1);
     sc.max_tiles = std::max<int64_t>(1, ceil_div(n, kSortTile));
     sc.lookback = c.take<unsigned long long>((size_t)sc.max_tiles * kBins);
     return sc;
-}
-
-static int clear_scratch(const SortScratch& sc, int64_t n, cudaStream_t s) {
-    MSC_TRY(cudaMemsetAsync(sc.hist, 0, (8 * kBins + kCounterWords) * sizeof(uint32_t), s));
-    const int64_t tiles = std::max<int64_t>(1, ceil_div(n, kSortTile));
-    MSC_TRY(cudaMemsetAsync(sc.lookback, 0, (size_t)tiles * kBins * sizeof(unsigned long long), s));
-    return MSC_OK;
 }
 
 // Clears the look-back words of the tiles that *d_n keys occupy (a sort
@@ -734,68 +639,6 @@ static int hist_grid(int64_t n) {
     return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)current_device().sms * 8));
 }
 
-int run_order(const float* f, int64_t n, int32_t* order, uint32_t* key_a, int32_t* id_a,
-              uint32_t* key_b, int32_t* id_b, const SortScratch& sc, int32_t* status,
-              cudaStream_t s) {
-    if (n <= 0) return MSC_OK;
-    int r = clear_scratch(sc, n, s);
-    if (r) return r;
-    if ((r = configure_hist())) return r;
-    {
-        TraceScope ts_("order.hist", s);
-        k_hist<uint32_t, true><<<hist_grid(n), 256, hist_smem(4), s>>>(nullptr, f, n, nullptr, 4, sc.hist, status);
-    }
-    MSC_LAUNCHED();
-    PassArgs<uint32_t> a{};
-    a.n = n;
-    a.status = status;
-    a.lookback = sc.lookback;
-    // pass 0: float field -> (key_a, id_a)
-    a.f_in = f;
-    a.keys_out = key_a;
-    a.vals_out = id_a;
-    a.hist = sc.hist;
-    a.shift = 0;
-    a.tile_counter = sc.tile_counters + 0;
-    a.epoch = 1;
-    if ((r = launch_pass<uint32_t, true, false>(a, n, s, "order.pass_first"))) return r;
-    // pass 1: a -> b ; pass 2: b -> a
-    uint32_t* kin = key_a;
-    int32_t* iin = id_a;
-    uint32_t* kout = key_b;
-    int32_t* iout = id_b;
-    for (int p = 1; p <= 2; ++p) {
-        a.f_in = nullptr;
-        a.keys_in = kin;
-        a.vals_in = iin;
-        a.keys_out = kout;
-        a.vals_out = iout;
-        a.hist = sc.hist + p * kBins;
-        a.shift = 8 * p;
-        a.tile_counter = sc.tile_counters + p;
-        a.epoch = (uint32_t)(p + 1);
-        if ((r = launch_pass<uint32_t, false, false>(a, n, s, "order.pass"))) return r;
-        std::swap(kin, kout);
-        std::swap(iin, iout);
-    }
-    // pass 3: a -> (id, position) pairs by id bucket in the free buffers,
-    // then order[id] = position
-    a.keys_in = kin;
-    a.vals_in = iin;
-    a.keys_out = nullptr;
-    a.vals_out = iout;
-    a.pair_pos = kout;
-    a.bucket_fill = sc.tile_counters + 8;
-    a.bucket_shift = bucket_shift(n);
-    a.hist = sc.hist + 3 * kBins;
-    a.shift = 24;
-    a.tile_counter = sc.tile_counters + 3;
-    a.epoch = 4;
-    if ((r = launch_pass<uint32_t, false, true>(a, n, s, "order.pass_last"))) return r;
-    // the pass's inputs are free now: the split writes there
-    return launch_pair_split_scatter(a.bucket_shift, iout, kout, iin, kin, sc.sub_fill, n, order, status, s);
-}
-
 void size_seg_sort_scratch(Sizer& s, int count, int64_t tiles) {
     s.take<uint32_t>((size_t)count * kSegPasses * kBins + kCounterWords);
     s.take<uint32_t>(ceil_div(std::max<int64_t>(tiles, 1) * kSortTile, kSubIds) + 1);
@@ -804,6 +647,7 @@ void size_seg_sort_scratch(Sizer& s, int count, int64_t tiles) {
 
 SortScratch carve_seg_sort_scratch(Carver& c, int count, int64_t tiles) {
     SortScratch sc;
+    sc.ord_cnt = nullptr;
     const size_t hist_words = (size_t)count * kSegPasses * kBins;
     sc.hist = c.take<uint32_t>(hist_words + kCounterWords);
     sc.tile_counters = sc.hist + hist_words;

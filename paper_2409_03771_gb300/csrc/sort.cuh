@@ -7,6 +7,8 @@
 namespace msc {
 
 struct SortScratch {
+    uint32_t* ord_cnt;                // vertex order: [256][kOrderMaxSuper] super-tile counts, [4][256]
+                                      // pass totals, [kOrderMaxBuckets][kOrderFillStride] bucket fills
     uint32_t* hist;                   // [8][256] digit histograms
     uint32_t* tile_counters;          // [8] dynamic tile ids, one per pass
     unsigned long long* lookback;     // [max_tiles][256] decoupled look-back words
@@ -15,6 +17,20 @@ struct SortScratch {
 };
 
 constexpr int kSortTile = 4096;       // keys per onesweep tile
+constexpr int kOrderMaxSuper = 8192;  // super-tiles (runs of consecutive tiles) of a vertex-order pass
+constexpr int kOrderMaxBuckets = 256; // id buckets the last order pass files pairs into
+constexpr int kOrderFillStride = 32;  // words between bucket fill counters (one 128-byte line each)
+constexpr size_t kOrderCntWords = (size_t)256 * kOrderMaxSuper + 4 * 256 + kOrderMaxBuckets * kOrderFillStride;
+
+// Width of the id buckets of the order's last pass: 2^19 ids at least, at
+// most kOrderMaxBuckets buckets.
+int order_bucket_shift(int64_t n);
+
+// Inverse permutation of the (id, position) pairs filed by id bucket
+// (bucket b holds the ids [b << shift, (b + 1) << shift)): order[id] =
+// position, through sub-buckets of 2^15 ids (ids2 / pos2: n-entry scratch).
+int order_invert(int shift, const int32_t* ids, const uint32_t* pos, int32_t* ids2, uint32_t* pos2,
+                 uint32_t* sub_fill, int64_t n, int32_t* order, int32_t* status, cudaStream_t s);
 
 // Bytes of scratch (hist + counters + look-back) for up to n keys.
 void size_sort_scratch(Sizer& s, int64_t n);

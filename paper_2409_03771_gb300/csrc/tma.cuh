@@ -67,6 +67,17 @@ __device__ __forceinline__ void tma_load_3d(void* dst, const CUtensorMap* map, i
         : "memory");
 }
 
+// 1D bulk copy (TMA, no tensor map) of `bytes` from global memory to this
+// CTA's shared memory, completing on `bar` (both addresses 16-byte
+// aligned, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+            smem_addr(dst)),
+        "l"(reinterpret_cast<uint64_t>(src)), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
 // Host: encode a 3D tensor map of 1- or 4-byte integers over a (nx, ny, nz)
 // array (x fastest), box (bx, by, bz), zero fill out of bounds.  Returns
 // false when TMA cannot describe the array (base not 16-byte aligned, row
