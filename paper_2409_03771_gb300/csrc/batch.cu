@@ -209,7 +209,7 @@ __global__ void k_batch_bound(const uint32_t* __restrict__ ext, const int32_t* _
 }
 
 // first[i] = #distinct pairs whose minimum lies before instance i (lower
-// bound of off_i * total among the sorted keys asc * total + desc);
+// bound of off_i << sh among the sorted keys (asc << sh) | desc);
 // num_cells[i] = first[i + 1] - first[i].
 __device__ __forceinline__ int64_t lower_bound_u64(const unsigned long long* a, int64_t K,
                                                    unsigned long long x) {
@@ -222,15 +222,13 @@ __device__ __forceinline__ int64_t lower_bound_u64(const unsigned long long* a, 
 }
 
 __global__ void k_batch_first(const unsigned long long* __restrict__ keys, const uint32_t* ctl,
-                              const int32_t* __restrict__ off, int count, int64_t total, int32_t* first,
+                              const int32_t* __restrict__ off, int count, int sh, int32_t* first,
                               int32_t* num_cells) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= count) return;
     const int64_t K = ctl[3];
-    const int64_t a = lower_bound_u64(keys, K, (unsigned long long)off[i] * (unsigned long long)total);
-    const int64_t b = i + 1 < count
-                          ? lower_bound_u64(keys, K, (unsigned long long)off[i + 1] * (unsigned long long)total)
-                          : K;
+    const int64_t a = lower_bound_u64(keys, K, (unsigned long long)off[i] << sh);
+    const int64_t b = i + 1 < count ? lower_bound_u64(keys, K, (unsigned long long)off[i + 1] << sh) : K;
     first[i] = (int32_t)a;
     num_cells[i] = (int32_t)(b - a);
 }
@@ -340,8 +338,8 @@ int run_batch(void* ws, size_t ws_bytes, const Layout& L, const DevLayout& d, co
     }
     {
         TraceScope ts_("batch.first", s);
-        k_batch_first<<<(unsigned)ceil_div(L.count, kThreads), kThreads, 0, s>>>(keys, d.ctl, d.off, L.count,
-                                                                                  L.total, d.first, B.num_cells);
+        k_batch_first<<<(unsigned)ceil_div(L.count, kThreads), kThreads, 0, s>>>(
+            keys, d.ctl, d.off, L.count, ms_pair_shift(L.total), d.first, B.num_cells);
     }
     MSC_LAUNCHED();
     // 5. instance-local ids

@@ -174,7 +174,11 @@ def test_compress_bad_pointer_is_reported(m):
 # Morse-Smale ids
 
 
-@pytest.mark.parametrize("n,nmin,nmax", [(1, 1, 1), (1000, 3, 7), (200003, 40, 900), (65536, 5000, 6000)])
+@pytest.mark.parametrize("n,nmin,nmax", [(1, 1, 1), (1000, 3, 7), (200003, 40, 900), (65536, 5000, 6000),
+                                         # tables past 2^20 slots: ranks by chunks of minimum ids,
+                                         # and the sort when a chunk or one minimum has too many pairs
+                                         (2_000_003, 300_000, 300_000), (2_000_003, 50, 200_000),
+                                         (1_500_007, 3, 1_000_000)])
 def test_ms_id(m, oracle_mod, n, nmin, nmax):
     rng = np.random.default_rng(n + nmin)
     ids = rng.permutation(n)
