@@ -199,10 +199,10 @@ def jump_activity(msc, fields, dims, dev):
 # step's sizes (n = grid vertices, nm / nnz = mesh vertices / CSR entries).
 def algorithmic_bytes(label, n, nm, nnz):
     table = {
-        "order.hist": 4 * n,             # read f
-        "order.pass_first": 12 * n,      # read f, write (key, id)
-        "order.pass": 16 * n,            # read and write (key, id)
-        "order.pass_last": 16 * n,       # read (key, id), write (id, position) pairs
+        "order.up": 4 * n,               # read the pass's keys (or f)
+        "order.down_first": 12 * n,      # read f, write (key, id)
+        "order.down": 16 * n,            # read and write (key, id)
+        "order.down_last": 16 * n,       # read (key, id), write (id, position) pairs
         "order.split": 16 * n,           # read the pairs, write them by sub-bucket of 2^15 ids
         "order.scatter": 12 * n,         # read the pairs, write order
         "steepest.grid": 12 * n,         # read order, write asc + desc
@@ -213,10 +213,22 @@ def algorithmic_bytes(label, n, nm, nnz):
         "mesh.init": 4 * nm,             # write label = v
         "mesh.link": 24 * nm,            # read row[v], row[v+1], two columns, write two hooks
         "mesh.flatten": 8 * nm,          # read and write every label
-        # mesh.hook reads only the edges of vertices outside the dominant
-        # component: data-dependent, no fixed algorithmic figure
+        # order.scan, the MS-id table passes (occupancy, chunk ranks) and
+        # mesh.hook move data-dependent amounts: no fixed algorithmic figure
     }
     return table.get(label)
+
+
+# Stages of the step: a stage's achieved bandwidth is the sum of its
+# kernels' algorithmic bytes over the sum of their device times.
+STAGES = {
+    "order": "order.",
+    "steepest": "steepest.",
+    "compress": "compress.",
+    "msid": "msid.",
+    "cc.mask": "cc.",
+    "cc.mesh": "mesh.",
+}
 
 
 # ---------------------------------------------------------------------------
@@ -425,7 +437,27 @@ def run_ours(args):
             "traffic": None if tb is None else tb * (nm if label.startswith("mesh") else n),
             "algorithmic_bytes": round(b), "avg_launch_ms": round(tot / cnt, 4),
             "share_of_step": round(tot / args.steps / ms, 4)}
-    roofline = next(iter(rooflines.values()), None)  # the kernel with the largest share
+    roofline = dict(next(iter(rooflines.values()))) if rooflines else None  # the kernel with the largest share
+    # every stage with its share of the step; the spec kernels
+    # (stencil, pointer jumping) by name
+    stage_list = []
+    for name, prefix in STAGES.items():
+        labels = [k for k in trace if k.startswith(prefix)]
+        t = sum(trace[k][1] for k in labels) / args.steps
+        known = [k for k in labels if per_launch_bytes(k, trace[k][0]) is not None]
+        b = sum(per_launch_bytes(k, trace[k][0]) * trace[k][0] for k in known) / args.steps
+        tk = sum(trace[k][1] for k in known) / args.steps
+        e = {"stage": name, "ms_per_step": round(t, 4), "share_of_step": round(t / ms, 4),
+             "kernels": sorted(labels, key=lambda k: -trace[k][1])}
+        if tk > 0:
+            e.update({"achieved": round(b / (tk / 1e3) / 1e9, 1), "frac": round(b / (tk / 1e3) / 1e9 / peak, 4),
+                      "bytes_counted_ms": round(tk, 4)})
+        stage_list.append(e)
+    stage_list.sort(key=lambda e: -e["share_of_step"])
+    if roofline:
+        roofline["stages"] = stage_list
+        roofline["north_star_kernels"] = {k: {kk: rooflines[k][kk] for kk in ("achieved", "frac", "avg_launch_ms")}
+                                          for k in ("steepest.grid", "compress.jump") if k in rooflines}
 
     out = {
         "metric": METRIC, "value": value, "unit": "vertices/s", "n_gpus": world, "steps": args.steps,

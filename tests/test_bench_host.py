@@ -8,7 +8,8 @@ import bench
 
 def test_algorithmic_bytes_scale_with_the_sizes():
     n, nm, nnz = 1 << 20, 1 << 16, 1 << 18
-    assert bench.algorithmic_bytes("order.pass", n, nm, nnz) == 16 * n
+    assert bench.algorithmic_bytes("order.down", n, nm, nnz) == 16 * n
+    assert bench.algorithmic_bytes("order.up", n, nm, nnz) == 4 * n
     assert bench.algorithmic_bytes("steepest.grid", n, nm, nnz) == 12 * n
     assert bench.algorithmic_bytes("mesh.flatten", n, nm, nnz) == 8 * nm
     assert bench.algorithmic_bytes("mesh.hook", n, nm, nnz) is None  # data-dependent
@@ -32,3 +33,9 @@ def test_sources_sha_depends_on_the_named_file_only():
     assert a == bench.sources_sha(["compress.cu"])
     assert a != bench.sources_sha(["sort.cu"])
     assert len(a) == 16
+
+
+def test_every_stage_prefix_matches_a_traced_label_family():
+    labels = ["order.up", "order.down", "steepest.grid", "compress.jump", "msid.insert", "cc.local", "mesh.link"]
+    for name, prefix in bench.STAGES.items():
+        assert any(l.startswith(prefix) for l in labels), name
