@@ -482,7 +482,7 @@ def run_ours(args):
         "stages_ms_per_step": stages,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        out["cpu_baseline"] = cpu_baseline(f_smooth, f_noise, mask, E)
+        out["cpu_baseline"] = cpu_baseline(f_smooth, f_noise, mask, E, row, col, (seg_out, cells, lab, mlab))
     if not args.no_adjacency:
         out["adjacency"] = adjacency_bench(dev, dims, [
             ("smooth", "desc", seg_out[0][2], n, None, 0), ("smooth", "ms", seg_out[0][3], int(cells[0].item()), None, 0),
@@ -866,7 +866,48 @@ def oracle_step(sample):
     return verts
 
 
-def cpu_baseline(f_smooth, f_noise, mask, E):
+def paper_omp_step(f_smooth, f_noise, mask, E, row, col, gpu_out=None):
+    """The paper's shared-memory method (Alg. 1 / Alg. 3, OpenMP, all host
+    cores) on the full step: both fields, the mask, the mesh.  With the GPU's
+    outputs of the same step, also whether every output is identical."""
+    import numpy as np
+
+    from oracle import paper_omp
+
+    paper_omp.build()
+    dims = (E, E, E)
+    host = [f_smooth.cpu().numpy(), f_noise.cpu().numpy(), mask.cpu().numpy(), row.cpu().numpy(),
+            col.cpu().numpy()]
+    stage = [0.0] * 4
+    t0 = time.perf_counter()
+    segs = []
+    for f in host[:2]:
+        r = paper_omp.segment_grid(f, dims)
+        stage = [a + b for a, b in zip(stage, r[5])]
+        segs.append(r)
+    t1 = time.perf_counter()
+    lab = paper_omp.cc_grid(host[2], dims, 6)
+    t2 = time.perf_counter()
+    mlab = paper_omp.cc_csr(host[3], host[4])
+    t3 = time.perf_counter()
+    out = {"value": (3 * E ** 3 + host[3].size - 1) / (t3 - t0), "unit": "vertices/s",
+           "cores": paper_omp.threads(), "kind": "paper method: Alg. 1 and Alg. 3, OpenMP",
+           "sample": "the full step: both 512^3 segmentations (with the order and cell ids), the 512^3 mask CC, "
+                     "the 256^3 mesh CC",
+           "seconds": round(t3 - t0, 2),
+           "stage_seconds": {"order": round(stage[0], 3), "steepest": round(stage[1], 3),
+                             "path_compression": round(stage[2], 3), "cell_ids": round(stage[3], 3),
+                             "cc_mask": round(t2 - t1, 3), "cc_mesh": round(t3 - t2, 3)}}
+    if gpu_out is not None:
+        so, cells, glab, gmlab = gpu_out
+        same = all(np.array_equal(segs[j][i], so[j][i].cpu().numpy()) for j in range(2) for i in range(4))
+        same &= [s_[4] for s_ in segs] == [int(c) for c in cells.cpu().tolist()]
+        same &= np.array_equal(lab, glab.cpu().numpy()) and np.array_equal(mlab, gmlab.cpu().numpy())
+        out["identical_to_gpu"] = bool(same)
+    return out
+
+
+def cpu_baseline(f_smooth, f_noise, mask, E, row=None, col=None, gpu_out=None):
     import oracle
 
     oracle.build()
@@ -874,8 +915,11 @@ def cpu_baseline(f_smooth, f_noise, mask, E):
     t0 = time.perf_counter()
     verts = oracle_step(sample)
     dt = time.perf_counter() - t0
-    return {"value": verts / dt, "unit": "vertices/s", "cores": 1, "kind": "oracle",
-            "sample": sample["desc"], "seconds": round(dt, 2)}
+    out = {"value": verts / dt, "unit": "vertices/s", "cores": 1, "kind": "oracle",
+           "sample": sample["desc"], "seconds": round(dt, 2)}
+    if row is not None:
+        out["paper_omp"] = paper_omp_step(f_smooth, f_noise, mask, E, row, col, gpu_out)
+    return out
 
 
 def run_reference(args):
