@@ -46,7 +46,7 @@ def parse_args():
     ap.add_argument("--no-batch", action="store_true", help="skip the 512-instance batched measurement")
     ap.add_argument("--batch-count", type=int, default=512)
     ap.add_argument("--no-serve", action="store_true", help="skip the served-request rate sweep")
-    ap.add_argument("--serve-requests", type=int, default=64, help="requests per arrival rate")
+    ap.add_argument("--serve-requests", type=int, default=1000, help="requests per arrival rate")
     ap.add_argument("--no-density", action="store_true", help="skip the 1024^3 mask-density sweep")
     ap.add_argument("--no-adjacency", action="store_true", help="skip the region-adjacency measurement")
     ap.add_argument("--copy-streams", type=int, default=1, help="copy streams per direction in the e2e leg")
@@ -597,49 +597,79 @@ def batch_bench(dev, count=512, reps=5):
 
 
 SERVE_RATES = (100, 300, 1000, 3000, 10000)
-SERVE_POOL = 48          # distinct seeded requests; request i takes pool[i % 48]
-SERVE_SEED0 = 5000
+SERVE_SEED0 = 5000       # request i at rate index r has seed SERVE_SEED0 + 100000 * r + i
 SERVE_BUDGET = 120 << 30
 
 
-def serve_pool(dev):
+def serve_inputs(count, seed0, dev):
+    """The requests of one rate, each with the input made from its own seed
+    (about 63 MB per request on average)."""
+    import torch
+
     import workloads
 
-    pool = []
-    for j in range(SERVE_POOL):
-        kind, edge, rng = workloads.serve_request(SERVE_SEED0 + j)
-        t = workloads.serve_field(kind, edge, rng, device=dev).reshape(-1).contiguous()
-        pool.append((kind, (edge, edge, edge), t))
-    return pool
+    jobs = [workloads.serve_job(seed0 + i, device=dev) for i in range(count)]
+    torch.cuda.synchronize()
+    return jobs
 
 
-def serve_run(msc, pool, rate, count, slots, group_max):
+def serve_run(msc, jobs, rate, slots, group_max):
+    """Poisson arrivals at `rate` of the prepared requests; a waiter thread
+    takes the results in submission order and releases them at once, so
+    that finished results do not fill the arena."""
+    import collections
+    import threading
+
     import numpy as np
 
     srv = msc.Server(SERVE_BUDGET, slots=slots, group_max_vertices=group_max)
     rng = np.random.default_rng(rate)
-    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=count))
-    tickets, verts = [], 0
+    arrivals = np.cumsum(rng.exponential(1.0 / rate, size=len(jobs)))
+    pending = collections.deque()
+    cv = threading.Condition()
+    results, state = [], {"done": False}
+
+    def waiter():
+        while True:
+            with cv:
+                cv.wait_for(lambda: pending or state["done"])
+                if not pending:
+                    return
+                tk = pending[0]
+            r = srv.wait(tk)
+            results.append((r.status, r.t_submit, r.t_start, r.t_done, r.group_size))
+            srv.release(tk)
+            with cv:
+                pending.popleft()
+
+    th = threading.Thread(target=waiter, daemon=True)
+    th.start()
+    verts, late = 0, 0
     t0 = time.perf_counter()
-    for i in range(count):
-        kind, dims, t = pool[i % len(pool)]
+    for i, (kind, dims, t) in enumerate(jobs):
         delay = t0 + arrivals[i] - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
-        tickets.append(srv.submit_segment(t, dims) if kind == "segment" else srv.submit_cc(t, dims, 6))
-        verts += t.numel()
-    res = [srv.wait(tk) for tk in tickets]
-    if any(r.status != msc.OK for r in res):
-        raise RuntimeError(f"served request failed: {[r.status for r in res if r.status]}")
-    lat = np.array([(r.t_done - r.t_submit) * 1e3 for r in res])
-    span = max(r.t_done for r in res) - min(r.t_submit for r in res)
-    out = {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
-           "vertices_per_s": verts / span, "requests_per_s": count / span,
-           "mean_group": round(float(np.mean([r.group_size for r in res])), 2)}
-    for tk in tickets:
-        srv.release(tk)
+        elif delay < -1e-3:
+            late += 1
+        tk = srv.submit_segment(t, dims) if kind == "segment" else srv.submit_cc(t, dims, 6)
+        verts += dims[0] * dims[1] * dims[2]
+        with cv:
+            pending.append(tk)
+            cv.notify_all()
+    with cv:
+        state["done"] = True
+        cv.notify_all()
+    th.join()
     srv.close()
-    return out
+    if any(r[0] != msc.OK for r in results):
+        raise RuntimeError(f"served request failed: {[r[0] for r in results if r[0]]}")
+    lat = np.array([(r[3] - r[1]) * 1e3 for r in results])
+    span = max(r[3] for r in results) - min(r[1] for r in results)
+    return {"p50_ms": round(float(np.percentile(lat, 50)), 3), "p99_ms": round(float(np.percentile(lat, 99)), 3),
+            "vertices_per_s": verts / span, "requests_per_s": len(jobs) / span,
+            "mean_group": round(float(np.mean([r[4] for r in results])), 2),
+            "submitted_late": late}
 
 
 def serve_bench(dev, count):
@@ -647,27 +677,30 @@ def serve_bench(dev, count):
 
     import paper_2409_03771_gb300 as msc
 
-    t0 = time.time()
-    pool = serve_pool(dev)
-    torch.cuda.synchronize()
-    gen_s = time.time() - t0
-    serve_run(msc, pool, 1000, 8, 4, 1 << 21)  # warm-up: library state, allocator
-    rates = []
+    warm = serve_inputs(16, SERVE_SEED0 + 900000, dev)
+    serve_run(msc, warm, 1000, 4, 1 << 21)  # warm-up: library state, allocator
+    del warm
+    rates, gen_s = [], 0.0
     with ClockSampler(dev.index) as clk:
-        for rate in SERVE_RATES:
-            row = {"rate": rate}
-            row.update(serve_run(msc, pool, rate, count, slots=4, group_max=1 << 21))
-            row["plain"] = serve_run(msc, pool, rate, count, slots=1, group_max=0)
+        for ri, rate in enumerate(SERVE_RATES):
+            t0 = time.time()
+            jobs = serve_inputs(count, SERVE_SEED0 + 100000 * ri, dev)
+            gen_s += time.time() - t0
+            row = {"rate": rate, "input_gb": round(sum(t.numel() * t.element_size() for _, _, t in jobs) / 2**30, 1)}
+            row.update(serve_run(msc, jobs, rate, 4, 1 << 21))
+            row["plain"] = serve_run(msc, jobs, rate, 1, 0)
             rates.append(row)
-    seg = [t.numel() for k, _, t in pool if k == "segment"]
-    cc = [t.numel() for k, _, t in pool if k == "cc"]
+            del jobs
+            torch.cuda.empty_cache()
     return {
-        "workload": (f"Poisson arrivals, {count} requests per rate, drawn from {SERVE_POOL} seeded requests "
-                     f"(seeds {SERVE_SEED0}..{SERVE_SEED0 + SERVE_POOL - 1}): 70% MS segmentation of a cube with "
-                     f"edge log-uniform in [32, 512], 30% 6-conn mask CC with edge log-uniform in [64, 768]"),
-        "budget_gb": SERVE_BUDGET >> 30, "server": "4 stream slots, segmentations <= 2^21 vertices batched",
+        "workload": (f"Poisson arrivals, {count} requests per rate, each with its own seeded input (made before "
+                     "the rate's run): 70% MS segmentation of a cube with edge log-uniform in [32, 512], 30% "
+                     "6-conn mask CC with edge log-uniform in [64, 768]; the same requests for the server and for "
+                     "the plain path"),
+        "budget_gb": SERVE_BUDGET >> 30,
+        "server": ("4 slots, each a high-priority stream (requests >= 2^24 vertices) and a low-priority one; "
+                   "segmentations <= 2^21 vertices batched, drawn from the next 64 waiting requests"),
         "plain": "1 slot, one request per launch sequence, no batching",
-        "pool_mean_vertices": {"segment": int(sum(seg) / max(1, len(seg))), "cc": int(sum(cc) / max(1, len(cc)))},
         "latency": "host submit to completion seen by the server (completion callback)",
         "rates": rates, "input_gen_s": round(gen_s, 1), "clocks": clk.summary(),
     }

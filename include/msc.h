@@ -360,20 +360,22 @@ MSC_API int msc_batch_autotune(const msc_grid* grids, int32_t count, const float
  * result is exactly what the single-request entry point returns for the
  * same input, alone or in any mix.
  *
- * Scheduling: a server thread takes requests in arrival order.  A request
- * is admitted when one of `slots` CUDA streams is free and its device
+ * Scheduling: a server thread takes requests in arrival order.  The head
+ * of the queue is admitted when one of `slots` slots is free and its device
  * memory (outputs + workspace, from an arena of `hbm_budget` bytes
- * allocated at creation) fits; admission never skips ahead, so no request
- * starves.  Consecutive waiting segmentation requests of at most
- * `group_max_vertices` vertices each are admitted together and run as one
- * batched launch (msc_batch_segment over a packed copy of their inputs);
- * larger requests and CC requests run on their own.  A batched launch
- * that reports a device error (e.g. a NaN in one field) is re-run request
- * by request, so every request gets the status it would get alone.  Work
- * on different
- * slots overlaps on the GPU; a request that arrives while others run is
- * admitted as soon as a slot and memory free up.  Results stay in the
- * arena until msc_server_release. */
+ * allocated at creation) fits, so no request starves.  When the head is a
+ * segmentation of at most `group_max_vertices` vertices, the segmentations
+ * of at most that size among the next 64 waiting requests are admitted
+ * with it (larger requests keep their places) and run as one batched launch
+ * (msc_batch_segment over a packed copy of their inputs); larger requests
+ * and CC requests run on their own.  A batched launch that reports a
+ * device error (e.g. a NaN in one field) is re-run request by request, so
+ * every request gets the status it would get alone.  Work on different
+ * slots overlaps on the GPU; each slot has a high-priority stream for
+ * requests of at least 2^24 vertices and a low-priority one for the rest,
+ * so that smaller work fills idle SMs around the large requests.  A
+ * request that arrives while others run is admitted as soon as a slot and
+ * memory free up.  Results stay in the arena until msc_server_release. */
 
 #define MSC_JOB_SEGMENT 1
 #define MSC_JOB_CC_MASK 2

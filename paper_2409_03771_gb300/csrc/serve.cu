@@ -1,13 +1,17 @@
 // Request server with continuous batching (include/msc.h, msc_server_*).
 //
 // One scheduler thread owns admission.  Requests wait in a FIFO; the head
-// is admitted when a slot (a CUDA stream) is free and its device memory
-// fits in the arena, never skipping ahead.  Consecutive small segmentation
-// requests at the head are admitted together and run as one batched
-// launch over a packed copy of their inputs; every other request runs on
-// its own.  Completion is signalled by a host function enqueued after the
-// request's work on its stream (it only takes a mutex and notifies), and
-// the scheduler then frees the slot; a request's outputs stay in the arena
+// is admitted when a slot is free and its device memory fits in the arena,
+// so no request starves.  When the head is a small segmentation, the small
+// segmentations among the next kLookAhead waiting requests join it (larger
+// requests keep their places) and run as one batched launch over a packed
+// copy of their inputs; every other request runs on its own.  A slot has
+// two streams: requests of at least kBigRequest vertices -- the ones that
+// set the tail latency -- run on the high-priority one, so that work
+// overlapping them on other slots fills idle SMs instead of slowing them.
+// Completion is signalled by a host function enqueued after the request's
+// work on its stream (it only takes a mutex and notifies), and the
+// scheduler then frees the slot; a request's outputs stay in the arena
 // until msc_server_release.  CUDA work is issued outside the state lock.
 #include <cuda_runtime.h>
 
@@ -28,6 +32,8 @@ namespace msc {
 namespace {
 
 constexpr int kMaxGroup = 256;        // requests in one batched launch
+constexpr size_t kLookAhead = 64;     // waiting requests a group may be drawn from
+constexpr int64_t kBigRequest = int64_t(1) << 24;  // vertices: high-priority stream
 constexpr int64_t kGroupTotal = 1 << 28;  // vertices in one batched launch
 constexpr size_t kAlign = 256;
 
@@ -105,7 +111,8 @@ struct Req {
 };
 
 struct Slot {
-    cudaStream_t stream = nullptr;
+    cudaStream_t stream = nullptr;     // low priority: batched and smaller requests
+    cudaStream_t stream_hi = nullptr;  // high priority: requests of >= kBigRequest vertices
     int32_t* h_info = nullptr;  // pinned: [0] status, [1 + i] cells of request i
     bool busy = false;
 };
@@ -140,6 +147,7 @@ struct msc_server {
     std::vector<Launch*> completed;
     uint64_t next_ticket = 1;
     int running = 0, finished = 0;
+    int big_running = 0;  // launches of >= kBigRequest vertices on the GPU
 };
 
 namespace msc {
@@ -152,6 +160,7 @@ struct Launch {
     Block* block;
     int host_error = MSC_OK;  // a launch that failed on the host
     double t_done = 0;
+    bool hi = false;          // issued on the slot's high-priority stream
 };
 
 void CUDART_CB on_done(void* p) {  // CUDA host function: no CUDA calls here
@@ -177,7 +186,7 @@ struct BlockCarver {
 // Enqueue the work of an admitted launch on its slot (no lock held).
 int issue(msc_server* S, Launch* L) {
     Slot& sl = S->slots[L->slot];
-    cudaStream_t st = sl.stream;
+    cudaStream_t st = L->hi ? sl.stream_hi : sl.stream;
     BlockCarver c{S->base + L->block->off};
     const int k = (int)L->reqs.size();
     int r = MSC_OK;
@@ -243,6 +252,7 @@ int issue(msc_server* S, Launch* L) {
 
 void finish(msc_server* S, Launch* L) {  // lock held
     Slot& sl = S->slots[L->slot];
+    S->big_running -= L->hi;
     const int k = (int)L->reqs.size();
     if (k > 1 && L->host_error == MSC_OK && sl.h_info[0] != MSC_OK) {
         // A batched launch shares one status word: re-run its requests one
@@ -286,35 +296,38 @@ bool groupable(const msc_server* S, const Req* q) {
 }
 
 // Pick the next launch from the head of the queue (lock held); nullptr if
-// the head does not fit now.
+// the head does not fit now.  A small segmentation at the head takes the
+// small segmentations among the next kLookAhead requests with it.
 Launch* admit(msc_server* S, int slot) {
     Req* head = S->queue.front();
-    std::vector<Req*> take{head};
+    std::vector<size_t> take{0};  // queue positions
     size_t bytes = solo_bytes(head->job, head->n);
+    auto group_bytes = [&](const std::vector<size_t>& pos) {
+        std::vector<msc_grid> grids;
+        int64_t total = 0;
+        for (size_t i : pos) {
+            grids.push_back(S->queue[i]->job.g);
+            total += S->queue[i]->n;
+        }
+        const int k = (int)pos.size();
+        return 5 * align_up((size_t)total * 4) + 2 * kAlign + align_up((size_t)k * 4) +
+               align_up(msc_batch_workspace_bytes(grids.data(), k));
+    };
     if (groupable(S, head)) {
         int64_t total = head->n;
-        std::vector<msc_grid> grids{head->job.g};
-        for (size_t i = 1; i < S->queue.size() && (int)take.size() < kMaxGroup; ++i) {
+        const size_t window = std::min(S->queue.size(), kLookAhead + 1);
+        for (size_t i = 1; i < window && (int)take.size() < kMaxGroup; ++i) {
             Req* q = S->queue[i];
-            if (!groupable(S, q) || total + q->n > kGroupTotal) break;
-            take.push_back(q);
-            grids.push_back(q->job.g);
+            if (!groupable(S, q) || total + q->n > kGroupTotal) continue;  // keeps its place
+            take.push_back(i);
             total += q->n;
         }
         if (take.size() > 1) {
-            const int k = (int)take.size();
-            bytes = 5 * align_up((size_t)total * 4) + 2 * kAlign + align_up((size_t)k * 4) +
-                    align_up(msc_batch_workspace_bytes(grids.data(), k));
+            bytes = group_bytes(take);
             // shrink the group until it fits (at least the head alone)
             while (bytes > S->arena.capacity() - S->arena.used() && take.size() > 1) {
                 take.pop_back();
-                grids.pop_back();
-                total = 0;
-                for (Req* q : take) total += q->n;
-                const int kk = (int)take.size();
-                bytes = kk == 1 ? solo_bytes(head->job, head->n)
-                                : 5 * align_up((size_t)total * 4) + 2 * kAlign + align_up((size_t)kk * 4) +
-                                      align_up(msc_batch_workspace_bytes(grids.data(), kk));
+                bytes = take.size() == 1 ? solo_bytes(head->job, head->n) : group_bytes(take);
             }
         }
     }
@@ -325,27 +338,48 @@ Launch* admit(msc_server* S, int slot) {
         bytes = solo_bytes(head->job, head->n);
         if (!S->arena.alloc(bytes, &off)) return nullptr;
     }
-    Block* b = new Block{off, bytes, (int)take.size()};
-    Launch* L = new Launch{S, slot, take, b, MSC_OK, 0};
+    std::vector<Req*> reqs;
+    for (size_t i : take) reqs.push_back(S->queue[i]);
+    Block* b = new Block{off, bytes, (int)reqs.size()};
+    Launch* L = new Launch{S, slot, reqs, b, MSC_OK, 0};
+    L->hi = reqs.size() == 1 && head->n >= kBigRequest;
+    S->big_running += L->hi;
     const double t = now_s();
-    for (Req* q : take) {
+    for (Req* q : reqs) {
         q->block = b;
         q->t_start = t;
-        q->group = (int)take.size();
-        S->queue.pop_front();
+        q->group = (int)reqs.size();
     }
+    for (size_t j = take.size(); j-- > 0;) S->queue.erase(S->queue.begin() + (std::ptrdiff_t)take[j]);
     S->slots[slot].busy = true;
-    S->running += (int)take.size();
+    S->running += (int)reqs.size();
     return L;
+}
+
+// Under light load (a short queue) a large request runs without newcomers:
+// overlapping work would only slow the request that sets the tail latency.
+// Under load the queue grows and everything overlaps for throughput.  The
+// hold lifts when the large request completes or the queue grows (both
+// wake the scheduler).
+bool hold_back(const msc_server* S) {
+#ifdef MSC_SERVE_NO_HOLD
+    return false;
+#else
+    return S->big_running > 0 && S->queue.size() <= S->slots.size();
+#endif
 }
 
 void scheduler(msc_server* S, int device) {
     cudaSetDevice(device);
     std::unique_lock<std::mutex> lock(S->mu);
     for (;;) {
+        // every state in which the admission loop below admits nothing must
+        // make this predicate false, or the thread would spin holding the
+        // lock that the completion callbacks need
         S->cv.wait(lock, [&] {
             return (S->stop && S->running == 0) || !S->completed.empty() ||
-                   (!S->stop && !S->queue.empty() && free_slot(S) >= 0 && S->failed_version != S->mem_version);
+                   (!S->stop && !S->queue.empty() && free_slot(S) >= 0 && S->failed_version != S->mem_version &&
+                    !hold_back(S));
         });
         if (!S->completed.empty()) {
             for (Launch* L : S->completed) finish(S, L);
@@ -356,7 +390,7 @@ void scheduler(msc_server* S, int device) {
         if (S->stop) continue;
         std::vector<Launch*> launches;
         int slot;
-        while (!S->queue.empty() && (slot = free_slot(S)) >= 0) {
+        while (!S->queue.empty() && (slot = free_slot(S)) >= 0 && !hold_back(S)) {
             Launch* L = admit(S, slot);
             if (!L) {
                 S->failed_version = S->mem_version;  // retry after a release
@@ -414,14 +448,17 @@ msc_server* msc_server_create(size_t hbm_budget, int32_t slots, int64_t group_ma
     S->arena.reset(hbm_budget);
     S->group_max = group_max_vertices;
     S->slots.resize(slots);
-    bool ok = true;
+    int lo_prio = 0, hi_prio = 0;
+    bool ok = cudaDeviceGetStreamPriorityRange(&lo_prio, &hi_prio) == cudaSuccess;
     for (Slot& sl : S->slots) {
-        ok = ok && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithPriority(&sl.stream, cudaStreamNonBlocking, lo_prio) == cudaSuccess;
+        ok = ok && cudaStreamCreateWithPriority(&sl.stream_hi, cudaStreamNonBlocking, hi_prio) == cudaSuccess;
         ok = ok && cudaMallocHost(&sl.h_info, (1 + kMaxGroup) * sizeof(int32_t)) == cudaSuccess;
     }
     if (!ok) {
         for (Slot& sl : S->slots) {
             if (sl.stream) cudaStreamDestroy(sl.stream);
+            if (sl.stream_hi) cudaStreamDestroy(sl.stream_hi);
             if (sl.h_info) cudaFreeHost(sl.h_info);
         }
         cudaFree(S->base);
@@ -520,7 +557,9 @@ void msc_server_destroy(msc_server* s) {
     if (s->thread.joinable()) s->thread.join();  // returns once running work completed
     for (Slot& sl : s->slots) {
         cudaStreamSynchronize(sl.stream);
+        cudaStreamSynchronize(sl.stream_hi);
         cudaStreamDestroy(sl.stream);
+        cudaStreamDestroy(sl.stream_hi);
         cudaFreeHost(sl.h_info);
     }
     for (auto& kv : s->reqs) {

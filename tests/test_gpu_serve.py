@@ -109,6 +109,30 @@ def test_small_served_requests_match_the_oracle(m, inputs):
     srv.close()
 
 
+def test_small_segmentations_group_past_a_large_request(m):
+    """With the only slot busy, the queue holds small, large, small, small,
+    CC: the small segmentations run as one launch, the large request keeps
+    its place behind the head, and every output equals the request alone."""
+    srv = m.Server(8 * GiB, slots=1, group_max_vertices=1 << 16)
+    blocker = seg_field((160, 160, 160), 80)
+    queue = [("seg", (20, 20, 20), seg_field((20, 20, 20), 81)),
+             ("seg", (100, 100, 100), seg_field((100, 100, 100), 82)),
+             ("seg", (24, 18, 22), seg_field((24, 18, 22), 83)),
+             ("seg", (16, 16, 16), seg_field((16, 16, 16), 84)),
+             ("cc", (40, 40, 40), cc_mask((40, 40, 40), 85))]
+    tb = srv.submit_segment(blocker, (160, 160, 160))
+    tickets = [submit(srv, *x) for x in queue]
+    res = [srv.wait(t) for t in tickets]
+    assert all(r.status == m.OK for r in res)
+    assert [r.group_size for r in res] == [3, 1, 3, 3, 1]
+    assert res[1].t_start >= res[0].t_start  # the large request was not overtaken by its own group's head
+    for t, x in zip(tickets, queue):
+        same(srv.outputs(t), solo(m, *x))
+        srv.release(t)
+    srv.release(tb)
+    srv.close()
+
+
 def test_budget_admission_waits_for_release(m):
     dims = (96, 96, 96)
     f1, f2 = seg_field(dims, 1), seg_field(dims, 2)
@@ -158,9 +182,10 @@ def test_error_in_a_batched_group_stays_with_its_request(m):
 
 def test_requests_arriving_while_others_run_are_admitted(m):
     """A stream of arrivals spread over time: later requests are admitted
-    while earlier ones are still on the GPU (their run intervals overlap)."""
+    while earlier ones are still on the GPU (their run intervals overlap).
+    The first request is just below the size that runs without newcomers."""
     srv = m.Server(16 * GiB, slots=4, group_max_vertices=1 << 16)
-    dims_big = (256, 256, 256)
+    dims_big = (255, 255, 255)
     big = seg_field(dims_big, 3)
     small = [seg_field((24, 24, 24), 60 + i) for i in range(6)]
     t_big = srv.submit_segment(big, dims_big)
@@ -174,6 +199,24 @@ def test_requests_arriving_while_others_run_are_admitted(m):
     for t, f in zip(ts, small):
         assert torch.equal(srv.outputs(t)["asc"], m.segment(f, (24, 24, 24))[1])
         srv.release(t)
+    srv.release(t_big)
+    srv.close()
+
+
+def test_a_large_request_runs_without_newcomers_under_light_load(m):
+    """A request of >= 2^24 vertices on the GPU and a short queue: a small
+    request that arrives meanwhile starts only after the large one is done."""
+    srv = m.Server(16 * GiB, slots=4, group_max_vertices=1 << 16)
+    dims_big = (256, 256, 256)  # 2^24 vertices
+    big = seg_field(dims_big, 4)
+    small = seg_field((24, 24, 24), 90)
+    t_big = srv.submit_segment(big, dims_big)
+    t_small = srv.submit_segment(small, (24, 24, 24))
+    rb, rs = srv.wait(t_big), srv.wait(t_small)
+    assert rb.status == m.OK and rs.status == m.OK
+    assert rs.t_start >= rb.t_done
+    assert torch.equal(srv.outputs(t_small)["ms"], m.segment(small, (24, 24, 24))[3])
+    srv.release(t_small)
     srv.release(t_big)
     srv.close()
 

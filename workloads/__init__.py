@@ -217,3 +217,29 @@ def serve_field(kind: str, edge: int, rng, device="cpu"):
     if kind == "cc":
         return (f > 0.3).to(torch.uint8)
     return f
+
+
+def serve_job(seed: int, device="cpu"):
+    """A served request with its own seeded input: (kind, dims, tensor) with
+    the kind and cube edge of ``serve_request(seed)`` and, from the same
+    generator, 8 Gaussians (sigma 4..12 scaled by edge / 64) evaluated in
+    float32 as one (nz*ny x 8) @ (8 x nx) product of the separable factors
+    -- a single write pass, so that a request's input can be made just
+    before it is submitted.  CC requests get the mask (field > 0.3)."""
+    kind, edge, rng = serve_request(seed)
+    dims = (edge,) * 3
+    g = edge / 64.0
+    centres, sigmas, amps, _ = gaussian_params(dims, 8, (4.0 * g, 12.0 * g), None, rng=rng)
+    dev = torch.device(device)
+    r = torch.arange(edge, dtype=torch.float32, device=dev)
+    c = torch.as_tensor(centres, dtype=torch.float32, device=dev)
+    k = torch.as_tensor(-1.0 / (2.0 * sigmas * sigmas), dtype=torch.float32, device=dev)[:, None]
+    a = torch.as_tensor(amps, dtype=torch.float32, device=dev)
+    ex = torch.exp(k * (r[None, :] - c[:, 0:1]) ** 2)
+    ey = torch.exp(k * (r[None, :] - c[:, 1:2]) ** 2)
+    ez = torch.exp(k * (r[None, :] - c[:, 2:3]) ** 2)
+    m = (a[:, None, None] * ez[:, :, None] * ey[:, None, :]).reshape(len(amps), -1)
+    f = (m.t() @ ex).reshape(-1)
+    if kind == "cc":
+        return kind, dims, (f > 0.3).to(torch.uint8)
+    return kind, dims, f
