@@ -195,6 +195,39 @@ def jump_activity(msc, fields, dims, dev):
     return total
 
 
+def link_probe(dev, nbytes=1 << 30, reps=3):
+    """Pinned host <-> device copy bandwidth (GB/s) over the host link: each
+    direction alone, and both at once on two streams (the end-to-end leg
+    runs both directions together)."""
+    import torch
+
+    h_a = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    h_b = torch.empty(nbytes, dtype=torch.uint8).pin_memory()
+    d_a = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    d_b = torch.empty(nbytes, dtype=torch.uint8, device=dev)
+    s1, s2 = torch.cuda.Stream(dev), torch.cuda.Stream(dev)
+
+    def timed(jobs):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(reps):
+            for st, fn in jobs:
+                with torch.cuda.stream(st):
+                    fn()
+        torch.cuda.synchronize()
+        return time.perf_counter() - t0
+
+    up = lambda: d_a.copy_(h_a, non_blocking=True)
+    down = lambda: h_b.copy_(d_b, non_blocking=True)
+    timed([(s1, up), (s2, down)])  # warm-up
+    t_up = timed([(s1, up)])
+    t_down = timed([(s2, down)])
+    t_both = timed([(s1, up), (s2, down)])
+    gb = reps * nbytes / 1e9
+    return {"h2d_alone": round(gb / t_up, 1), "d2h_alone": round(gb / t_down, 1),
+            "both_total": round(2 * gb / t_both, 1)}
+
+
 # Algorithmic bytes per launch of each traced kernel, as functions of the
 # step's sizes (n = grid vertices, nm / nnz = mesh vertices / CSR entries).
 def algorithmic_bytes(label, n, nm, nnz):
@@ -352,6 +385,8 @@ def run_ours(args):
         s_in = [torch.cuda.Stream(dev) for _ in range(ncs)]
         s_out = [torch.cuda.Stream(dev) for _ in range(ncs)]
         ev_in = [[torch.cuda.Event() for _ in range(ncs)] for _ in range(2)]
+        # per timed step: first / last copy of each direction (timing events)
+        dir_ev = []
         ev_done = [torch.cuda.Event() for _ in range(2)]
         ev_out = [[torch.cuda.Event() for _ in range(ncs)] for _ in range(2)]
         for e in ev_done + [x for xs in ev_out for x in xs]:
@@ -367,13 +402,18 @@ def run_ours(args):
                     out.append((d1[a:a + step_elems], h1[a:a + step_elems]))
             return out
 
-        def e2e_step(i):
+        def e2e_step(i, timing=False):
             b = i % 2
+            te = [torch.cuda.Event(enable_timing=True) for _ in range(4)] if timing else None
             for j in range(ncs):
                 s_in[j].wait_event(ev_done[b])  # step i-2 no longer reads d_in[b]
+            if timing:
+                te[0].record(s_in[0])
             for j, (d, h) in enumerate(pieces(d_in[b], h_in)):
                 with torch.cuda.stream(s_in[j % ncs]):
                     d.copy_(h, non_blocking=True)
+            if timing:
+                te[1].record(s_in[0])
             for j in range(ncs):
                 ev_in[b][j].record(s_in[j])
                 stream.wait_event(ev_in[b][j])
@@ -382,9 +422,14 @@ def run_ours(args):
             ev_done[b].record(stream)
             for j in range(ncs):
                 s_out[j].wait_event(ev_done[b])
+            if timing:
+                te[2].record(s_out[0])
             for j, (h, d) in enumerate(pieces(h_out[b], flat(d_out[b]))):
                 with torch.cuda.stream(s_out[j % ncs]):
                     h.copy_(d, non_blocking=True)
+            if timing:
+                te[3].record(s_out[0])
+                dir_ev.append(te)
             for j in range(ncs):
                 ev_out[b][j].record(s_out[j])
 
@@ -398,7 +443,7 @@ def run_ours(args):
         for j in range(ncs):
             s_in[j].wait_event(ev0)
         for i in range(ee):
-            e2e_step(i)
+            e2e_step(i, timing=(ncs == 1))
         for b in range(2):
             for j in range(ncs):
                 stream.wait_event(ev_out[b][j])
@@ -407,8 +452,18 @@ def run_ours(args):
         barrier()
         check_status("e2e")
         e_ms, e_value = replica_throughput(ev0.elapsed_time(ev1) / ee, verts, world, dev)
+        # achieved rate of each direction's copies within the steps (one
+        # copy stream per direction: first to last piece on that stream)
+        dirs = {}
+        if dir_ev:
+            up = sorted(e[0].elapsed_time(e[1]) for e in dir_ev)
+            down = sorted(e[2].elapsed_time(e[3]) for e in dir_ev)
+            dirs = {"h2d_ms_median": round(up[len(up) // 2], 2), "d2h_ms_median": round(down[len(down) // 2], 2),
+                    "h2d_gbs": round(h2d / (up[len(up) // 2] / 1e3) / 1e9, 1),
+                    "d2h_gbs": round(d2h / (down[len(down) // 2] / 1e3) / 1e9, 1)}
         e2e = {"value": e_value, "unit": "vertices/s", "ms_per_step": e_ms, "h2d_bytes_per_step": h2d,
-               "d2h_bytes_per_step": d2h,
+               "d2h_bytes_per_step": d2h, "copy_streams_per_direction": ncs, "within_steps": dirs,
+               "link_probe": link_probe(dev),
                "pipelined": (f"inputs and outputs in pieces of <= 64 MiB over {ncs} copy streams per direction, "
                              "compute on its own stream, double-buffered; every step copies all inputs and outputs")}
         del d_in, d_out, h_out
