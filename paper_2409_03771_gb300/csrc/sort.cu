@@ -27,6 +27,7 @@
 
 #include "radix.cuh"
 #include "sort.cuh"
+#include "tma.cuh"
 
 namespace msc {
 #ifdef MSC_DEBUG_BOUNDS
@@ -437,23 +438,69 @@ constexpr int kSplitChunk = 4096;
 constexpr int kSplitPer = kSplitChunk / kSplitThreads;  // 8
 constexpr int kMaxSub = 1 << 8;  // sub-buckets per bucket (shift <= 23)
 
-__global__ void __launch_bounds__(kSplitThreads) k_pair_split(const int32_t* __restrict__ ids_in,
-                                                              const uint32_t* __restrict__ pos_in, int64_t n,
-                                                              int shift, uint32_t* sub_fill,
-                                                              int32_t* __restrict__ ids_out,
-                                                              uint32_t* __restrict__ pos_out, int32_t* status) {
-    __shared__ int32_t s_id[kSplitChunk];
-    __shared__ uint32_t s_pos[kSplitChunk];
-    __shared__ uint32_t s_cnt[kMaxSub];   // counts, then chunk-local starts
-    __shared__ uint32_t s_base[kMaxSub];  // first slot of the chunk's run in each sub-bucket
-    __shared__ uint32_t s_w[kSplitThreads / 32];
+// The chunk's pairs arrive by 1D TMA bulk copy into one half of a shared
+// double buffer while the previous chunk is filed (plain loads for a ragged
+// last chunk or unaligned arrays); they are counted per sub-bucket,
+// regrouped in place and written out as runs.
+constexpr size_t kSplitSmem = (size_t)2 * 2 * kSplitChunk * 4 + (2 * kMaxSub + 32) * 4 + 2 * 8;
+
+__global__ void __launch_bounds__(kSplitThreads, 2) k_pair_split(const int32_t* __restrict__ ids_in,
+                                                                 const uint32_t* __restrict__ pos_in, int64_t n,
+                                                                 int shift, int use_tma, uint32_t* sub_fill,
+                                                                 int32_t* __restrict__ ids_out,
+                                                                 uint32_t* __restrict__ pos_out, int32_t* status) {
+    extern __shared__ __align__(16) uint8_t smem[];
+    uint32_t* buf = reinterpret_cast<uint32_t*>(smem);     // [2][ids kSplitChunk | positions kSplitChunk]
+    uint32_t* s_cnt = buf + 2 * 2 * kSplitChunk;            // [kMaxSub] counts, then chunk-local starts
+    uint32_t* s_base = s_cnt + kMaxSub;                     // [kMaxSub] first slot of the run in each sub-bucket
+    uint32_t* s_w = s_base + kMaxSub;                       // [32]
+    uint64_t* mbar = reinterpret_cast<uint64_t*>(s_w + 32); // [2]
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int nsub = 1 << (shift - kSubLog2);
-    for (int64_t c0 = (int64_t)blockIdx.x * kSplitChunk; c0 < n; c0 += (int64_t)gridDim.x * kSplitChunk) {
+    const int64_t nchunks = (n + kSplitChunk - 1) / kSplitChunk;
+    if ((int64_t)blockIdx.x >= nchunks) return;  // block-uniform
+    if (tid == 0) {
+        mbar_init(&mbar[0], 1);
+        mbar_init(&mbar[1], 1);
+        fence_mbar_init();
+    }
+    __syncthreads();
+    auto by_tma = [&](int64_t c) { return use_tma && (c + 1) * kSplitChunk <= n; };
+    auto issue = [&](int64_t c, int slot) {  // one thread
+        if (c >= nchunks || !by_tma(c)) return;
+        uint32_t* dst = buf + slot * 2 * kSplitChunk;
+        mbar_expect_tx(&mbar[slot], 2 * kSplitChunk * 4);
+        bulk_load(dst, ids_in + c * kSplitChunk, kSplitChunk * 4, &mbar[slot]);
+        bulk_load(dst + kSplitChunk, pos_in + c * kSplitChunk, kSplitChunk * 4, &mbar[slot]);
+    };
+    if (tid == 0) issue(blockIdx.x, 0);
+    int it = 0;
+    for (int64_t c = blockIdx.x; c < nchunks; c += gridDim.x, ++it) {
+        const int slot = it & 1;
+        uint32_t* bi = buf + slot * 2 * kSplitChunk;
+        uint32_t* bp = bi + kSplitChunk;
+        if (tid == 0) issue(c + gridDim.x, slot ^ 1);
+        const int64_t c0 = c * kSplitChunk;
         const int cnt = (int)min((int64_t)kSplitChunk, n - c0);
         const int64_t s0 = (c0 >> shift) << shift;  // first id of the chunk's bucket
         for (int i = tid; i < nsub; i += kSplitThreads) s_cnt[i] = 0;
-        __syncthreads();
+        if (by_tma(c)) {
+            const bool ok = mbar_wait(&mbar[slot], (uint32_t)(it >> 1) & 1u, kSpinLimit);
+            if (__syncthreads_or(!ok)) {  // a copy never landed: report, let the prefetch finish, stop
+                if (tid == 0) {
+                    record_error(status, MSC_ERR_INTERNAL);
+                    if (c + gridDim.x < nchunks && by_tma(c + gridDim.x))
+                        mbar_wait(&mbar[slot ^ 1], (uint32_t)((it + 1) >> 1) & 1u, kSpinLimit);
+                }
+                return;
+            }
+        } else {
+            for (int i = tid; i < cnt; i += kSplitThreads) {
+                bi[i] = (uint32_t)ids_in[c0 + i];
+                bp[i] = pos_in[c0 + i];
+            }
+            __syncthreads();
+        }
         int32_t id[kSplitPer];
         uint32_t ps[kSplitPer], rank[kSplitPer];
 #pragma unroll
@@ -461,8 +508,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_pair_split(const int32_t* __r
             const int i = tid + k * kSplitThreads;
             id[k] = -1;
             if (i < cnt) {
-                id[k] = __ldcs(ids_in + c0 + i);
-                ps[k] = __ldcs(pos_in + c0 + i);
+                id[k] = (int32_t)bi[i];
+                ps[k] = bp[i];
                 const int64_t off = (int64_t)id[k] - s0;
                 MSC_GUARD(off >= 0 && off < (int64_t(1) << shift), status, -106)
                 rank[k] = atomicAdd(&s_cnt[off >> kSubLog2], 1u);
@@ -471,8 +518,8 @@ __global__ void __launch_bounds__(kSplitThreads) k_pair_split(const int32_t* __r
         __syncthreads();
         // chunk-local exclusive starts over the nsub (<= 256) sub-buckets, and
         // the chunk's reservation in each of them
-        const uint32_t c = tid < nsub ? s_cnt[tid] : 0u;
-        uint32_t incl = c;
+        const uint32_t cc = tid < nsub ? s_cnt[tid] : 0u;
+        uint32_t incl = cc;
 #pragma unroll
         for (int o = 1; o < 32; o <<= 1) {
             const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
@@ -483,28 +530,33 @@ __global__ void __launch_bounds__(kSplitThreads) k_pair_split(const int32_t* __r
         uint32_t before = 0;
         for (int w = 0; w < warp; ++w) before += s_w[w];
         if (tid < nsub) {
-            s_base[tid] = c ? atomicAdd(&sub_fill[(s0 >> kSubLog2) + tid], c) : 0u;
-            s_cnt[tid] = before + incl - c;
+            s_base[tid] = cc ? atomicAdd(&sub_fill[(s0 >> kSubLog2) + tid], cc) : 0u;
+            s_cnt[tid] = before + incl - cc;
         }
         __syncthreads();
+        // regroup in place: every pair of the chunk was read before the barriers above
 #pragma unroll
         for (int k = 0; k < kSplitPer; ++k)
             if (id[k] >= 0) {
                 const uint32_t j = s_cnt[(uint32_t)(id[k] - s0) >> kSubLog2] + rank[k];
-                s_id[j] = id[k];
-                s_pos[j] = ps[k];
+                MSC_GUARD(j < (uint32_t)kSplitChunk, status, -109) {
+                    bi[j] = (uint32_t)id[k];
+                    bp[j] = ps[k];
+                }
             }
         __syncthreads();
         for (int i = tid; i < cnt; i += kSplitThreads) {
-            const int32_t v = s_id[i];
+            const int32_t v = (int32_t)bi[i];
             const int sub = (int)((uint32_t)(v - s0) >> kSubLog2);
-            const uint32_t slot = s_base[sub] + (uint32_t)i - s_cnt[sub];
-            const int64_t dst = s0 + ((int64_t)sub << kSubLog2) + slot;
-            MSC_GUARD(slot < (uint32_t)kSubIds && dst < n, status, -107) {
+            const uint32_t slot_ = s_base[sub] + (uint32_t)i - s_cnt[sub];
+            const int64_t dst = s0 + ((int64_t)sub << kSubLog2) + slot_;
+            MSC_GUARD(slot_ < (uint32_t)kSubIds && dst < n, status, -107) {
                 ids_out[dst] = v;
-                pos_out[dst] = s_pos[i];
+                pos_out[dst] = bp[i];
             }
         }
+        // this buffer is refilled by a bulk copy (async proxy) two chunks on
+        fence_proxy_async_smem();
         __syncthreads();
     }
 }
@@ -539,18 +591,20 @@ int launch_pair_split_scatter(int shift, const int32_t* ids, const uint32_t* pos
                               uint32_t* sub_fill, int64_t n, int32_t* order, int32_t* status, cudaStream_t s) {
     const int sms = current_device().sms;
     MSC_TRY(cudaMemsetAsync(sub_fill, 0, (size_t)(ceil_div(n, kSubIds) + 1) * sizeof(uint32_t), s));
-    {
-        const int64_t chunks = ceil_div(n, kSplitChunk);
-        TraceScope ts_("order.split", s);
-        k_pair_split<<<(unsigned)std::min<int64_t>(chunks, (int64_t)sms * 4), kSplitThreads, 0, s>>>(
-            ids, pos, n, shift, sub_fill, ids2, pos2, status);
-    }
-    MSC_LAUNCHED();
     static int configured_dev = -1;
     if (configured_dev != current_device().id) {
         MSC_TRY(cudaFuncSetAttribute(k_pair_scatter_local, cudaFuncAttributeMaxDynamicSharedMemorySize, kSubIds * 4));
+        MSC_TRY(cudaFuncSetAttribute(k_pair_split, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSplitSmem));
         configured_dev = current_device().id;
     }
+    {
+        const int64_t chunks = ceil_div(n, kSplitChunk);
+        const int use_tma = ((uintptr_t)ids & 15) == 0 && ((uintptr_t)pos & 15) == 0;
+        TraceScope ts_("order.split", s);
+        k_pair_split<<<(unsigned)std::min<int64_t>(chunks, (int64_t)sms * 2), kSplitThreads, kSplitSmem, s>>>(
+            ids, pos, n, shift, use_tma, sub_fill, ids2, pos2, status);
+    }
+    MSC_LAUNCHED();
     const int64_t nsub = ceil_div(n, kSubIds);
     {
         TraceScope ts_("order.scatter", s);
