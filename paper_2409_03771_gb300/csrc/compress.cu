@@ -43,7 +43,10 @@ struct JumpPair {
     uint32_t* roots;  // optional: roots[i] += #vertices of array i that point at themselves
 };
 
-constexpr int kHops = 3;  // pointer hops followed per vertex and sweep
+#ifndef MSC_JUMP_HOPS
+#define MSC_JUMP_HOPS 4
+#endif
+constexpr int kHops = MSC_JUMP_HOPS;  // pointer hops followed per vertex and sweep
 constexpr int kPerThread = 8;  // vertices per thread and chunk
 constexpr int kChunkV = kThreads * kPerThread;
 

@@ -51,6 +51,7 @@ namespace {
 constexpr int kT = 256;                // threads per block
 constexpr int kI = MSC_ORD_ITEMS;      // keys per thread and tile
 constexpr int kTile = kT * kI;  // keys per tile (4096)
+static_assert(kI % 4 == 0, "digits are packed four to a word");
 constexpr int kW = kT / kWarp;  // 8 warps
 constexpr int kB = kRadixBins;  // 256 digits
 constexpr uint32_t kWaitLimit = 1u << 22;  // mbarrier polls before giving up (~0.3 s)
@@ -206,19 +207,14 @@ struct DownArgs {
 };
 
 // Shared memory of k_ord_down: two tile buffers of (key, value) words,
-// warp histograms (16-bit), per-digit words, scan scratch, bucket words,
-// two mbarriers.
+// warp histograms (16-bit; after the count, each warp's tile-local start),
+// per-digit words, scan scratch, bucket words, two mbarriers.
 constexpr size_t kBufWords = 2 * kTile;
-constexpr size_t kDownSmem = 2 * kBufWords * 4 + kW * kB * 2 + 3 * kB * 4 + 32 * 4 + 2 * kB * 4 + 2 * 8;
+constexpr size_t kDownSmem = 2 * kBufWords * 4 + kW * kB * 2 + 2 * kB * 4 + 32 * 4 + 2 * kB * 4 + 2 * 8;
 
-// Lanes of the warp holding the same digit as this lane (valid lanes
-// only): one match instruction, whose cost grows with the number of
-// distinct digits in the warp, or eight ballots, whose cost does not.
-template <bool MATCH>
-__device__ __forceinline__ uint32_t same_digit_lanes(uint32_t d, bool valid) {
-    if constexpr (MATCH) return __match_any_sync(0xffffffffu, valid ? d : 0x100u | (threadIdx.x & 31));
-    else return digit_peers(d, valid);
-}
+// Lanes of the warp holding the same digit as this lane: one match
+// instruction, whose cost grows with the number of distinct digits in the
+// warp, or eight ballots, whose cost does not (digit_peers in radix.cuh).
 
 template <bool FROM_F, bool BUCKET, int SHIFT>
 __global__ void __launch_bounds__(kT, MSC_ORD_MIN_BLOCKS) k_ord_down(const DownArgs a) {
@@ -226,8 +222,7 @@ __global__ void __launch_bounds__(kT, MSC_ORD_MIN_BLOCKS) k_ord_down(const DownA
     uint32_t* buf = reinterpret_cast<uint32_t*>(smem);                     // [2][kTile words | kTile words]
     uint16_t* s_wh = reinterpret_cast<uint16_t*>(buf + 2 * kBufWords);     // [kW][kB]
     uint32_t* s_run = reinterpret_cast<uint32_t*>(s_wh + kW * kB);         // [kB] next output position
-    uint32_t* s_excl = s_run + kB;                                         // [kB] tile-local digit start
-    uint32_t* s_delta = s_excl + kB;                                       // [kB] output pos - staged pos
+    uint32_t* s_delta = s_run + kB;                                        // [kB] output pos - staged pos
     uint32_t* s_misc = s_delta + kB;                                       // [32] scan scratch
     uint32_t* s_bcnt = s_misc + 32;                                        // [kB] BUCKET
     uint32_t* s_bbase = s_bcnt + kB;                                       // [kB] BUCKET
@@ -309,14 +304,21 @@ __global__ void __launch_bounds__(kT, MSC_ORD_MIN_BLOCKS) k_ord_down(const DownA
         // stable rank among the warp's equal digits: earlier keys of the warp
         // (its 16-bit counter) + lower lanes of this step
         uint32_t rk[kI / 2];
-        auto rank_tile = [&](auto match_tag) {
+        uint32_t dg[kI / 4];  // the digits of the thread's keys, four to a word
+        // FULL: every key of the tile is valid (all but a ragged last tile)
+        auto rank_tile = [&](auto match_tag, auto full_tag) {
             constexpr bool MATCH = decltype(match_tag)::value;
+            constexpr bool FULL = decltype(full_tag)::value;
 #pragma unroll
             for (int k = 0; k < kI; ++k) {
                 const int li = wb + 32 * k;
-                const bool valid = li < cnt;
+                const bool valid = FULL || li < cnt;
                 const uint32_t d = valid ? digit_of<SHIFT>(key_at(li)) : 0u;
-                const uint32_t peers = same_digit_lanes<MATCH>(d, valid);
+                dg[k / 4] = (k & 3) ? (dg[k / 4] | d << (8 * (k & 3))) : d;
+                uint32_t peers;
+                if constexpr (MATCH) peers = __match_any_sync(0xffffffffu, valid ? d : 0x100u | lane);
+                else if constexpr (FULL) peers = digit_peers_all(d);
+                else peers = digit_peers(d, valid);
                 const uint32_t lower = __popc(peers & lt);
                 const uint32_t before = wh[d];
                 if (valid && lower == 0) wh[d] = (uint16_t)(before + __popc(peers));
@@ -325,21 +327,27 @@ __global__ void __launch_bounds__(kT, MSC_ORD_MIN_BLOCKS) k_ord_down(const DownA
                 __syncwarp();
             }
         };
-        if (use_match) rank_tile(std::true_type{});
-        else rank_tile(std::false_type{});
+        if (cnt == kTile) {
+            if (use_match) rank_tile(std::true_type{}, std::true_type{});
+            else rank_tile(std::false_type{}, std::true_type{});
+        } else {
+            if (use_match) rank_tile(std::true_type{}, std::false_type{});
+            else rank_tile(std::false_type{}, std::false_type{});
+        }
         if constexpr (BUCKET) s_bcnt[tid] = 0u;
         __syncthreads();
-        {   // digit tid: warp counts -> warp-exclusive prefixes; tile start; output start
-            uint32_t run = 0;
+        {   // digit tid: warp counts -> tile-local start of each warp's run of
+            // the digit (16-bit: at most kTile); output start of the tile's run
+            uint32_t pre[kW], run = 0;
 #pragma unroll
             for (int w = 0; w < kW; ++w) {
-                const uint32_t c = s_wh[w * kB + tid];
-                s_wh[w * kB + tid] = (uint16_t)run;
-                run += c;
+                pre[w] = run;
+                run += s_wh[w * kB + tid];
             }
             const uint32_t excl = block_scan_256(run, s_misc) - run;
+#pragma unroll
+            for (int w = 0; w < kW; ++w) s_wh[w * kB + tid] = (uint16_t)(excl + pre[w]);
             const uint32_t g = s_run[tid];
-            s_excl[tid] = excl;
             s_delta[tid] = g - excl;
             s_run[tid] = g + run;
         }
@@ -360,8 +368,8 @@ __global__ void __launch_bounds__(kT, MSC_ORD_MIN_BLOCKS) k_ord_down(const DownA
                 uint32_t lpos = 0;
                 if (li < cnt) {
                     const uint32_t kk = key_at(li);
-                    const uint32_t d = digit_of<SHIFT>(kk);
-                    lpos = s_excl[d] + wh[d] + ((rk[k / 2] >> (16 * (k & 1))) & 0xffffu);
+                    const uint32_t d = (dg[k / 4] >> (8 * (k & 3))) & 255u;
+                    lpos = wh[d] + ((rk[k / 2] >> (16 * (k & 1))) & 0xffffu);
                     MSC_GUARD(lpos < (uint32_t)kTile, a.status, -141) bv[lpos] = kk;
                 }
                 rk[k / 2] = (k & 1) ? ((rk[k / 2] & 0xffffu) | lpos << 16) : ((rk[k / 2] & 0xffff0000u) | lpos);
@@ -399,8 +407,8 @@ __global__ void __launch_bounds__(kT, MSC_ORD_MIN_BLOCKS) k_ord_down(const DownA
 #pragma unroll
             for (int k = 0; k < kI; ++k) {
                 const int li = wb + 32 * k;
-                const uint32_t d = li < cnt ? digit_of<SHIFT>(key_at(li)) : 0u;
-                ppos[k] = s_delta[d] + s_excl[d] + wh[d] + ((rk[k / 2] >> (16 * (k & 1))) & 0xffffu);
+                const uint32_t d = li < cnt ? (dg[k / 4] >> (8 * (k & 3))) & 255u : 0u;
+                ppos[k] = s_delta[d] + wh[d] + ((rk[k / 2] >> (16 * (k & 1))) & 0xffffu);
             }
             __syncwarp();
             for (int j = lane; j < kB / 2; j += 32) reinterpret_cast<uint32_t*>(wh)[j] = 0u;

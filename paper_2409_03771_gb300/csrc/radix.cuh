@@ -61,6 +61,18 @@ __device__ __forceinline__ uint32_t digit_peers(uint32_t d, bool valid) {
     return eq;
 }
 
+// The same for a warp whose 32 lanes all hold a valid digit.
+__device__ __forceinline__ uint32_t digit_peers_all(uint32_t d) {
+    uint32_t eq = 0xffffffffu;
+#pragma unroll
+    for (int b = 0; b < 8; ++b) {
+        const bool bit = (d >> b) & 1u;
+        const uint32_t bal = __ballot_sync(0xffffffffu, bit);
+        eq &= bit ? bal : ~bal;
+    }
+    return eq;
+}
+
 constexpr int kHistRun = 16;  // consecutive keys per thread in the histogram
 
 // Loads the float keys f[i0 .. i0+cnt) (cnt <= 16; the rest become 0)
