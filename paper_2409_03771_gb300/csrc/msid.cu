@@ -148,28 +148,54 @@ __device__ __forceinline__ uint32_t home_slot(uint32_t asc, unsigned long long k
 // `broke`: a pair is no longer within M of its base.  The probe resumes at
 // step i0 (slot h0), after the steps a caller made itself.
 constexpr uint32_t kNearProbes = 1024;
+static_assert(kPad % 4 == 0, "the table's slot count is a multiple of four");
 
 __device__ __forceinline__ uint32_t probe_insert(unsigned long long* keys, uint32_t cap, unsigned long long key,
                                                  uint32_t i0, uint32_t h0, bool& fresh, bool& broke,
                                                  int32_t* status) {
     const uint32_t lim = cap + kPad;
     uint32_t h = h0;
-    for (uint32_t i = i0; i < lim + kNearProbes; ++i) {
+    // One round trip reads the aligned group of four slots (one 32-byte
+    // sector) holding slot h and takes the first of slots h, h+1, ... in it
+    // that holds the key or is empty.  The steps stop exactly at kNearProbes
+    // and at the end of the table (lim, a multiple of four), so every insert
+    // of a key visits the same slots in the same order.
+    uint32_t i = i0;
+    while (i < lim + kNearProbes) {
         if (i == kNearProbes) {
             h = (uint32_t)mix64(key ^ 0x9e3779b97f4a7c15ull) & (cap - 1);
             broke = true;
         }
-        const unsigned long long k = keys[h];
-        if (k == key) return h;
-        if (k == kEmpty) {
-            const unsigned long long old = atomicCAS(&keys[h], kEmpty, key);
+        const uint32_t g0 = h & ~3u, start = h - g0;
+        const uint32_t end = i < kNearProbes ? min(4u, start + (kNearProbes - i)) : 4u;
+        const ulonglong2 lo = *reinterpret_cast<const ulonglong2*>(keys + g0);
+        const ulonglong2 hi = *reinterpret_cast<const ulonglong2*>(keys + g0 + 2);
+        const unsigned long long sl[4] = {lo.x, lo.y, hi.x, hi.y};
+        uint32_t q = 4;
+        unsigned long long v = 0;
+#pragma unroll
+        for (int j = 3; j >= 0; --j) {
+            if ((uint32_t)j >= start && (uint32_t)j < end && (sl[j] == key || sl[j] == kEmpty)) {
+                q = (uint32_t)j;
+                v = sl[j];
+            }
+        }
+        if (q == 4) {  // none in the group: on to the next one
+            i += end - start;
+            h = g0 + end;
+        } else {
+            const uint32_t slot = g0 + q;
+            if (v == key) return slot;
+            const unsigned long long old = atomicCAS(&keys[slot], kEmpty, key);
             if (old == kEmpty) {
                 fresh = true;
-                return h;
+                return slot;
             }
-            if (old == key) return h;
+            if (old == key) return slot;
+            i += q - start + 1;  // another key took the slot first
+            h = slot + 1;
         }
-        if (++h == lim) {
+        if (h == lim) {
             h = 0;
             broke = true;
         }
