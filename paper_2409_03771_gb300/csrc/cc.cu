@@ -33,7 +33,6 @@ namespace {
 constexpr int CX = 64, CY = 8, CZ = 8;
 constexpr int CT = CX * CY * CZ;  // 4096
 constexpr int kThreads = 256;
-constexpr int kPer = CT / kThreads;  // 16
 constexpr uint32_t kUnionLimit = 1u << 20;
 
 struct CcGrid {
@@ -41,6 +40,7 @@ struct CcGrid {
     int32_t tx, ty;
     int64_t ntiles;
     int conn;
+    int vec;  // nx % 8 == 0, mask 8-byte and label 16-byte aligned: rows move as 8-byte / 16-byte words
 };
 
 __device__ __forceinline__ void cc_tile_coords(const CcGrid& g, int64_t t, int& x0, int& y0, int& z0) {
@@ -138,6 +138,42 @@ __global__ void __launch_bounds__(kThreads) k_cc_local(const uint8_t* __restrict
     for (int64_t t = blockIdx.x; t < g.ntiles; t += gridDim.x) {
         int x0, y0, z0;
         cc_tile_coords(g, t, x0, y0, z0);
+        // the 64 row bitmasks
+        if (g.vec) {
+            // 8 lanes per row, 8 mask bytes per lane: byte j nonzero -> bit j
+            const int sub = lane & 7;
+#pragma unroll
+            for (int pass = 0; pass < 2; ++pass) {
+                const int r = warp * 4 + (lane >> 3) + 32 * pass;
+                const int ly = r & (CY - 1), lz = r / CY;
+                const int gy = y0 + ly, gz = z0 + lz, gx = x0 + 8 * sub;
+                uint32_t bits = 0;
+                if (gy < g.ny && gz < g.nz && gx < g.nx) {
+                    const uint2 w = *reinterpret_cast<const uint2*>(
+                        mask + (gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz)));
+                    // high bit of each byte set iff the byte is nonzero; then
+                    // the four high bits gathered into bits 28..31
+                    const uint32_t lo = (w.x | ((w.x & 0x7f7f7f7fu) + 0x7f7f7f7fu)) & 0x80808080u;
+                    const uint32_t hi = (w.y | ((w.y & 0x7f7f7f7fu) + 0x7f7f7f7fu)) & 0x80808080u;
+                    bits = ((lo * 0x00204081u) >> 28) | (((hi * 0x00204081u) >> 28) << 4);
+                }
+                reinterpret_cast<uint8_t*>(s_row)[8 * r + sub] = (uint8_t)bits;
+            }
+            __syncthreads();
+            for (int r = warp; r < kRows; r += kThreads / 32) {
+                const uint64_t m = s_row[r];
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int x = lane + 32 * h;
+                    int lab = -1;
+                    if (m >> x & 1ull) {
+                        const uint64_t z = run_start_mask_below(m, x);
+                        lab = (z ? 64 - __clzll((long long)z) : 0) + CX * r;
+                    }
+                    s_l[x + CX * r] = lab;
+                }
+            }
+        } else {
         // rows: warp w takes rows w, w + 8, ..., 8 rows per warp
         for (int r = warp; r < kRows; r += kThreads / 32) {
             const int ly = r & (CY - 1), lz = r / CY;
@@ -161,6 +197,7 @@ __global__ void __launch_bounds__(kThreads) k_cc_local(const uint8_t* __restrict
                 }
                 s_l[x + CX * r] = lab;
             }
+        }
         }
         __syncthreads();
         // unite runs of neighbouring rows, once per overlap segment
@@ -200,25 +237,49 @@ __global__ void __launch_bounds__(kThreads) k_cc_local(const uint8_t* __restrict
             }
         }
         __syncthreads();
-#pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int i = tid + k * kThreads;
-            if (s_l[i] >= 0) s_l[i] = find_s(s_l, i);
+        // every run start takes its root (four threads per row, a quarter
+        // of the row each); a voxel's entry names its run start
+        {
+            const int r = tid >> 2, q = tid & 3;
+            const uint64_t m = s_row[r];
+            uint64_t st = m & ~(m << 1) & (0xffffull << (16 * q));
+            while (st) {
+                const int xs = __ffsll((long long)st) - 1;
+                st &= st - 1;
+                s_l[xs + CX * r] = find_s(s_l, xs + CX * r);
+            }
         }
         __syncthreads();
+        // every voxel takes its run start's root: 16 threads per row, four
+        // consecutive voxels each, stored as one 16-byte word where the row
+        // allows
+        const int64_t tbase = x0 + (int64_t)g.nx * (y0 + (int64_t)g.ny * z0);
+        const int64_t nxy = (int64_t)g.nx * g.ny;
+        const int x = 4 * (tid & 15);
 #pragma unroll
-        for (int k = 0; k < kPer; ++k) {
-            const int i = tid + k * kThreads;
-            const int lx = i & (CX - 1), ly = (i / CX) & (CY - 1), lz = i / (CX * CY);
-            const int gx = x0 + lx, gy = y0 + ly, gz = z0 + lz;
-            if (gx < g.nx && gy < g.ny && gz < g.nz) {
-                int32_t out = -1;
-                const int r = s_l[i];
-                if (r >= 0) {
-                    const int rx = r & (CX - 1), ry = (r / CX) & (CY - 1), rz = r / (CX * CY);
-                    out = (int32_t)((x0 + rx) + (int64_t)g.nx * ((y0 + ry) + (int64_t)g.ny * (z0 + rz)));
+        for (int pass = 0; pass < kRows / 16; ++pass) {
+            const int r = (tid >> 4) + 16 * pass;
+            const int ly = r & (CY - 1), lz = r / CY;
+            if (y0 + ly >= g.ny || z0 + lz >= g.nz || x0 + x >= g.nx) continue;
+            int32_t out[4];
+#pragma unroll
+            for (int j = 0; j < 4; ++j) {
+                const int i = x + j + CX * r;
+                out[j] = -1;
+                const int ls = s_l[i];
+                if (ls >= 0) {
+                    const int rt = s_l[ls];
+                    const int rx = rt & (CX - 1), ry = (rt / CX) & (CY - 1), rz = rt / (CX * CY);
+                    out[j] = (int32_t)(tbase + rx + (int64_t)g.nx * ry + nxy * rz);
                 }
-                label[gx + (int64_t)g.nx * (gy + (int64_t)g.ny * gz)] = out;
+            }
+            int32_t* dst = label + tbase + x + (int64_t)g.nx * ly + nxy * lz;
+            if (g.vec) {
+                *reinterpret_cast<int4*>(dst) = make_int4(out[0], out[1], out[2], out[3]);
+            } else {
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (x0 + x + j < g.nx) dst[j] = out[j];
             }
         }
         __syncthreads();
@@ -465,6 +526,7 @@ int run_cc_mask(const uint8_t* mask, msc_grid gd, int conn, int32_t* label, int3
     g.ty = (int)ceil_div(gd.ny, CY);
     g.ntiles = (int64_t)g.tx * g.ty * ceil_div(gd.nz, CZ);
     g.conn = conn;
+    g.vec = gd.nx % 8 == 0 && ((uintptr_t)mask & 7) == 0 && ((uintptr_t)label & 15) == 0;
     const int64_t n = (int64_t)gd.nx * gd.ny * gd.nz;
     const int sms = current_device().sms;
     int occ = 1;
