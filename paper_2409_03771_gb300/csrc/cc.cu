@@ -30,6 +30,9 @@
 namespace msc {
 namespace {
 
+#ifndef MSC_CC_LOCAL_MIN_BLOCKS
+#define MSC_CC_LOCAL_MIN_BLOCKS 6
+#endif
 constexpr int CX = 64, CY = 8, CZ = 8;
 constexpr int CT = CX * CY * CZ;  // 4096
 constexpr int kThreads = 256;
@@ -130,7 +133,7 @@ __device__ __forceinline__ uint64_t run_start_mask_below(uint64_t m, int x) {
     return ~m & ((x ? (~0ull >> (64 - x)) : 0ull));
 }
 
-__global__ void __launch_bounds__(kThreads) k_cc_local(const uint8_t* __restrict__ mask, const CcGrid g,
+__global__ void __launch_bounds__(kThreads, MSC_CC_LOCAL_MIN_BLOCKS) k_cc_local(const uint8_t* __restrict__ mask, const CcGrid g,
                                                        int32_t* __restrict__ label) {
     __shared__ int s_l[CT];
     __shared__ uint64_t s_row[kRows];
