@@ -321,6 +321,7 @@ int run_batch(void* ws, size_t ws_bytes, const Layout& L, const DevLayout& d, co
         int32_t* arr[2] = {B.asc, B.desc};
         CompressTune ct;
         ct.build_shift = T.build_shift;
+        ct.fill_lists = false;  // the tuned threshold
         ct.trusted = true;  // made by the batched stencil: in range, acyclic
         r = run_compress(arr, 2, total, sc, B.status, s, ct);
         if (r) return r;

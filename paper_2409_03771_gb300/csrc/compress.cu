@@ -4,19 +4,22 @@
 // d[u] may already see this sweep's write, which only lengthens the jump.
 //
 // GPU form: one launch per sweep over all vertices (eight vertices per
-// thread, lane-consecutive).  Each vertex follows up to three hops per sweep
-// (d[v] <- d[d[d[d[v]]]]), so a sweep at least quadruples every pointer's
-// reach for the same 8 bytes of pointer read and write per vertex; the
-// extra reads mostly hit the cache.  Launched ceil(log4 n) + 2 times.
-// Each sweep counts
-// the vertices it changed; a sweep whose predecessor changed nothing
-// returns at once, so no host synchronisation is needed.  Once at most
-// n >> build_shift vertices changed, the sweep also appends the changed
-// vertices to an active list (block-aggregated atomics) and the following
-// sweeps walk only that list -- the GPU counterpart of the paper's
-// per-thread active lists.  A pointer cycle is reported as
-// MSC_ERR_NOT_CONVERGED: either a hop lands on its own vertex, or the last
-// sweep still changes something.
+// thread, lane-consecutive).  Each vertex follows up to kHops (4) hops per
+// sweep (d[v] <- d[d[d[d[d[v]]]]]), so a sweep at least quintuples every
+// pointer's reach for the same 8 bytes of pointer read and write per
+// vertex; the extra reads mostly hit the cache.  Launched ceil(log5 n) + 2
+// times.  Each sweep counts the vertices it changed; a sweep whose
+// predecessor changed nothing returns at once, so no host synchronisation
+// is needed.  A sweep also appends the vertices it changed to an active
+// list (block-aggregated atomics) once the previous sweep's count is at
+// most 1.5x the list's capacity (a vertex that did not move never moves
+// again, so the count can only fall); when the changes still overflow the
+// list, the next sweep walks all vertices instead.  The following sweeps
+// walk only the list -- the GPU counterpart of the paper's per-thread
+// active lists.  (With fill_lists off, the list is built only once at most
+// n >> build_shift vertices changed, which never overflows.)  A pointer
+// cycle is reported as MSC_ERR_NOT_CONVERGED: either a hop lands on its
+// own vertex, or the last sweep still changes something.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -104,15 +107,16 @@ __device__ __forceinline__ uint32_t jump_group(const int32_t* p, int32_t n, cons
 }
 
 template <bool CHECKED>
-__global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, int build_shift,
+__global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, uint32_t build_max,
                                                    int32_t* status) {
     const JumpArray A = blockIdx.y ? pr.a[1] : pr.a[0];
     const int32_t n = pr.n;
     int32_t* p = A.p;
     const uint32_t prev = step == 0 ? (uint32_t)n : A.ctl->cnt[step - 1];
     if (prev == 0) return;
-    const bool from_list = step > 0 && A.ctl->built[step - 1] != 0;
-    const bool build = prev <= ((uint32_t)n >> build_shift);
+    // the previous sweep's list is complete only if its changes fitted
+    const bool from_list = step > 0 && A.ctl->built[step - 1] != 0 && (int64_t)prev <= A.list_cap;
+    const bool build = prev <= build_max;
     if (build && blockIdx.x == 0 && threadIdx.x == 0) A.ctl->built[step] = 1u;
     int32_t* out_list = (step & 1) ? A.list1 : A.list0;
     const int32_t* in_list = (step & 1) ? A.list0 : A.list1;
@@ -190,8 +194,7 @@ __global__ void __launch_bounds__(kThreads) k_jump(const JumpPair pr, int step, 
 #pragma unroll
             for (int j = 0; j < kPerThread; ++j)
                 if (ch & (1u << j)) {
-                    MSC_GUARD((int64_t)off < A.list_cap, status, -122)
-                    out_list[off] = vid[j];
+                    if ((int64_t)off < A.list_cap) out_list[off] = vid[j];  // past it: the list is dropped
                     ++off;
                 }
             __syncthreads();
@@ -254,6 +257,8 @@ int run_compress(int32_t* const* ptrs, int count, int32_t n, const CompressScrat
         pr.a[i].list_cap = sc.list_cap;
     }
     const int build_shift = std::max(1, std::min(tune.build_shift, 30));
+    const int64_t fill_max = std::min<int64_t>(sc.list_cap + sc.list_cap / 2, UINT32_MAX);
+    const uint32_t build_max = tune.fill_lists ? (uint32_t)fill_max : ((uint32_t)n >> build_shift);
     auto kern = tune.trusted ? k_jump<false> : k_jump<true>;
     int occ = 1;
     MSC_TRY(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, kThreads, 0));
@@ -263,7 +268,7 @@ int run_compress(int32_t* const* ptrs, int count, int32_t n, const CompressScrat
     for (int st = 0; st < steps; ++st) {
         {
             TraceScope ts_("compress.jump", s);
-            kern<<<dim3(gx, count), kThreads, 0, s>>>(pr, st, build_shift, status);
+            kern<<<dim3(gx, count), kThreads, 0, s>>>(pr, st, build_max, status);
         }
         MSC_LAUNCHED();
     }
@@ -330,6 +335,7 @@ extern "C" MSC_API int msc_compress_noalloc(int32_t* ptr, int32_t n, int32_t* d_
     sc.lists = reinterpret_cast<int32_t*>(static_cast<unsigned char*>(base) + kNoAllocCtlBytes);
     msc::CompressTune tune;
     tune.build_shift = kNoAllocBuildShift;
+    tune.fill_lists = false;
     int32_t* arr[1] = {ptr};
     return msc::run_compress(arr, 1, n, sc, d_status, s, tune);
 }

@@ -15,13 +15,15 @@ struct JumpCtl {
 };
 
 struct CompressTune {
-    int build_shift = 3;   // build the active list once <= n >> build_shift changed
+    bool fill_lists = true;  // build the active list whenever the previous sweep's count is at
+                             // most 1.5x its capacity (an overflow leaves a full sweep next)
+    int build_shift = 3;     // fill_lists off: build it once <= n >> build_shift changed
     bool trusted = false;  // pointers from the stencil kernels: skip range / cycle tests
     uint32_t* roots = nullptr;  // roots[i] += #self-pointers of array i (first sweep)
 };
 
-// Sweeps launched for n vertices: ceil(log4 n) + 2 (enough for any forest
-// at a fourfold advance per sweep; more are needed only by a cycle).
+// Sweeps launched for n vertices: ceil(log5 n) + 2 (enough for any forest
+// at a fivefold advance per sweep; more are needed only by a cycle).
 int compress_steps(int64_t n);
 
 // Workspace pieces for `count` arrays of n entries.

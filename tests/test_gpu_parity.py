@@ -137,6 +137,32 @@ def test_compress_forests(m, oracle_mod, n, roots, span):
     np.testing.assert_array_equal(host(m.compress(cuda(ptr))), oracle_mod.walk_memo(ptr))
 
 
+def test_compress_active_list_overflow_falls_back(m, oracle_mod):
+    """30 % roots and 70 % of the vertices on 70 chains of 10 000: the first
+    sweep moves 70 %, which is under 1.5x the list's capacity (n/2), so the
+    second sweep builds a list; it moves nearly all of them again, more than
+    the list holds, so the third sweep must walk every vertex.  The per-sweep
+    counts the call leaves in its workspace show that path was taken."""
+    n = 1_000_000
+    rng = np.random.default_rng(11)
+    perm = rng.permutation(n).astype(np.int32)
+    ptr = np.empty(n, np.int32)
+    roots = perm[:300_000]
+    ptr[roots] = roots
+    chains = perm[300_000:].reshape(70, 10_000)
+    ptr[chains[:, 0]] = roots[:70]
+    ptr[chains[:, 1:]] = chains[:, :-1]
+    p = cuda(ptr)
+    ws = torch.zeros(m.msc_workspace_bytes(m.OP_COMPRESS, n), dtype=torch.uint8, device="cuda")
+    st = torch.zeros(1, dtype=torch.int32, device="cuda")
+    assert m.msc_compress(p, n, ws, ws.numel(), st) == 0
+    torch.cuda.synchronize()
+    assert int(st.item()) == 0
+    cnt = ws[:256].view(torch.int32).cpu().tolist()
+    assert 500_001 < cnt[0] <= 750_001 and cnt[1] > 500_001  # built at sweep 1, overflowed
+    np.testing.assert_array_equal(host(p), oracle_mod.walk_memo(ptr))
+
+
 def test_compress_keeps_inactive(m, oracle_mod):
     rng = np.random.default_rng(5)
     ptr = forest(100003, rng, 50, 100)
