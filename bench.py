@@ -141,16 +141,12 @@ class ClockSampler:
 
 
 def sources_sha(names):
-    """Hash of the kernel source files `names` (in the package's csrc), their
-    own headers and the device helpers every kernel includes (the public
-    header only declares entry points and is left out)."""
+    """Hash of the kernel source files `names` (in the package's csrc) and of
+    every device header there (a kernel's own header, the radix and TMA
+    helpers; the public header only declares entry points and is left out)."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2409_03771_gb300", "csrc")
-    files = ["common.cuh", "tma.cuh"]
-    for f in sorted(names):
-        files.append(f)
-        if os.path.exists(os.path.join(csrc, f[:-3] + ".cuh")):
-            files.append(f[:-3] + ".cuh")
+    files = sorted(f for f in os.listdir(csrc) if f.endswith(".cuh")) + sorted(names)
     for f in files:
         with open(os.path.join(csrc, f), "rb") as fh:
             h.update(f.encode() + fh.read())

@@ -9,7 +9,7 @@
 // rank under (f[v], v).
 //
 // Each pass is an upsweep / scan / downsweep over super-tiles (runs of S
-// consecutive 4096-key tiles), so no block ever waits for another:
+// consecutive 6144-key tiles), so no block ever waits for another:
 //   k_ord_up    counts the pass digit of every super-tile (run-length
 //               counted into warp-private shared histograms);
 //   k_ord_scan  one block per digit turns the super-tile counts into each
@@ -40,17 +40,17 @@ namespace msc {
 namespace {
 
 #ifndef MSC_ORD_ITEMS
-#define MSC_ORD_ITEMS 16
+#define MSC_ORD_ITEMS 24
 #endif
 #ifndef MSC_ORD_MIN_BLOCKS
-#define MSC_ORD_MIN_BLOCKS 3
+#define MSC_ORD_MIN_BLOCKS 2
 #endif
 #ifndef MSC_ORD_MATCH_MAX
 #define MSC_ORD_MATCH_MAX 64
 #endif
 constexpr int kT = 256;                // threads per block
 constexpr int kI = MSC_ORD_ITEMS;      // keys per thread and tile
-constexpr int kTile = kT * kI;  // keys per tile (4096)
+constexpr int kTile = kT * kI;  // keys per tile (6144)
 static_assert(kI % 4 == 0, "digits are packed four to a word");
 constexpr int kW = kT / kWarp;  // 8 warps
 constexpr int kB = kRadixBins;  // 256 digits
