@@ -82,6 +82,7 @@ __device__ __forceinline__ uint32_t jump_group(const int32_t* p, int32_t n, cons
     }
 #pragma unroll
     for (int h = 0; h < kHops; ++h) {
+        if (h > 0 && !__any_sync(0xffffffffu, live)) break;  // the warp's chains all ended
         int32_t w[kPerThread];
 #pragma unroll
         for (int j = 0; j < kPerThread; ++j) w[j] = (live >> j & 1u) ? p[d[j]] : 0;
