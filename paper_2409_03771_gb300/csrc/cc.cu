@@ -389,6 +389,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_flatten(int32_t* label, int64_
         // vertex (labels only decrease), so following it stays correct
 #pragma unroll
         for (int h = 0; h < kFlatHops; ++h) {
+            if (!__any_sync(0xffffffffu, open)) break;  // the warp's chains all ended
             int32_t w[kFlatPer];
 #pragma unroll
             for (int j = 0; j < kFlatPer; ++j) w[j] = (open >> j & 1u) ? label[r[j]] : 0;
