@@ -432,7 +432,7 @@ def run_ours(args):
         for i in range(4):  # untimed: the copy path and both buffer sets warm up
             e2e_step(i)
         torch.cuda.synchronize()
-        ee = max(2, min(args.steps, 6))
+        ee = max(2, args.steps)
         barrier()
         torch.cuda.synchronize()
         ev0.record(stream)
@@ -454,9 +454,14 @@ def run_ours(args):
         if dir_ev:
             up = sorted(e[0].elapsed_time(e[1]) for e in dir_ev)
             down = sorted(e[2].elapsed_time(e[3]) for e in dir_ev)
+            # step to step: the start of one step's input copies to the next one's
+            gaps = sorted(a[0].elapsed_time(b[0]) for a, b in zip(dir_ev, dir_ev[1:]))
             dirs = {"h2d_ms_median": round(up[len(up) // 2], 2), "d2h_ms_median": round(down[len(down) // 2], 2),
                     "h2d_gbs": round(h2d / (up[len(up) // 2] / 1e3) / 1e9, 1),
-                    "d2h_gbs": round(d2h / (down[len(down) // 2] / 1e3) / 1e9, 1)}
+                    "d2h_gbs": round(d2h / (down[len(down) // 2] / 1e3) / 1e9, 1),
+                    "step_ms_min": round(gaps[0], 2) if gaps else None,
+                    "step_ms_median": round(gaps[len(gaps) // 2], 2) if gaps else None,
+                    "step_ms_max": round(gaps[-1], 2) if gaps else None}
         e2e = {"value": e_value, "unit": "vertices/s", "ms_per_step": e_ms, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "copy_streams_per_direction": ncs, "within_steps": dirs,
                "link_probe": link_probe(dev),
