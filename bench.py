@@ -17,6 +17,7 @@ a bounded sample of the same workload.
 from __future__ import annotations
 
 import argparse
+import gc
 import hashlib
 import json
 import os
@@ -358,10 +359,11 @@ def run_ours(args):
     # step go in on copy streams, the step computes on its own stream, its
     # outputs come back on other copy streams; inputs and outputs are
     # double-buffered, so the copies of neighbouring steps overlap the
-    # compute.  Each direction's copies are cut into pieces of at most
-    # 64 MiB dealt round-robin over --copy-streams streams, so that several
-    # copy engines work at once.  Every step still copies all its inputs in
-    # and all its outputs out.
+    # compute.  With one copy stream per direction each array is one copy;
+    # with --copy-streams > 1 the copies are cut into pieces of at most 64 MiB
+    # dealt round-robin over the streams, so that several copy engines work
+    # at once.  Every step still copies all its inputs in and all its
+    # outputs out.
     e2e = None
     if not args.no_e2e:
         srcs = (f_smooth, f_noise, mask, row, col)
@@ -388,12 +390,16 @@ def run_ours(args):
         for e in ev_done + [x for xs in ev_out for x in xs]:
             e.record(stream)
 
+        # one copy per array on a single copy stream (fewer host calls per
+        # step); pieces of 64 MiB when several streams share the arrays
+        piece_bytes = (64 << 20) if ncs > 1 else (1 << 40)
+
         def pieces(dsts, srcs_):
-            """(dst, src) views of at most 64 MiB covering every pair."""
+            """(dst, src) views of at most piece_bytes covering every pair."""
             out = []
             for d, h in zip(dsts, srcs_):
                 d1, h1 = d.view(-1), h.view(-1)
-                step_elems = max(1, (64 << 20) // d1.element_size())
+                step_elems = max(1, piece_bytes // d1.element_size())
                 for a in range(0, d1.numel(), step_elems):
                     out.append((d1[a:a + step_elems], h1[a:a + step_elems]))
             return out
@@ -435,11 +441,13 @@ def run_ours(args):
         ee = max(2, args.steps)
         barrier()
         torch.cuda.synchronize()
+        gc.disable()  # no collector pause while the host enqueues the steps
         ev0.record(stream)
         for j in range(ncs):
             s_in[j].wait_event(ev0)
         for i in range(ee):
             e2e_step(i, timing=(ncs == 1))
+        gc.enable()
         for b in range(2):
             for j in range(ncs):
                 stream.wait_event(ev_out[b][j])
@@ -459,13 +467,15 @@ def run_ours(args):
             dirs = {"h2d_ms_median": round(up[len(up) // 2], 2), "d2h_ms_median": round(down[len(down) // 2], 2),
                     "h2d_gbs": round(h2d / (up[len(up) // 2] / 1e3) / 1e9, 1),
                     "d2h_gbs": round(d2h / (down[len(down) // 2] / 1e3) / 1e9, 1),
+                    "h2d_ms_max": round(up[-1], 2), "d2h_ms_max": round(down[-1], 2),
                     "step_ms_min": round(gaps[0], 2) if gaps else None,
                     "step_ms_median": round(gaps[len(gaps) // 2], 2) if gaps else None,
                     "step_ms_max": round(gaps[-1], 2) if gaps else None}
         e2e = {"value": e_value, "unit": "vertices/s", "ms_per_step": e_ms, "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": d2h, "copy_streams_per_direction": ncs, "within_steps": dirs,
                "link_probe": link_probe(dev),
-               "pipelined": (f"inputs and outputs in pieces of <= 64 MiB over {ncs} copy streams per direction, "
+               "pipelined": (("inputs and outputs one copy per array on one copy stream per direction, " if ncs == 1 else
+                              f"inputs and outputs in pieces of <= 64 MiB over {ncs} copy streams per direction, ") +
                              "compute on its own stream, double-buffered; every step copies all inputs and outputs")}
         del d_in, d_out, h_out
 
