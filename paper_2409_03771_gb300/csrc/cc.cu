@@ -364,13 +364,13 @@ __global__ void __launch_bounds__(kThreads) k_cc_merge(const CcGrid g, int32_t* 
 
 // Pointer jumping to the roots.  A thread takes 8 labels, lane-consecutive
 // (label c*2048 + j*256 + tid), and follows their chains hop by hop
-// together: 8 independent gathers in flight, and the 32 lanes of each
-// gather read neighbouring labels, whose roots are mostly shared.  The few
-// chains still open after kFlatHops hops finish one by one.  Once every
-// hook is done the root reached is the component minimum, so a plain store
-// of it cannot lose anything.
+// together until the warp's chains have all ended: 8 independent gathers
+// in flight, and the 32 lanes of each gather read neighbouring labels,
+// whose roots are mostly shared (the union-find before it halved the
+// paths, so chains are short).  Once every hook is done the root reached is
+// the component minimum, so a plain store of it cannot lose anything.
 constexpr int kFlatPer = 8;
-constexpr int kFlatHops = 4;
+constexpr int kFlatHops = (int)kUnionLimit;  // bound only: a forest's chains end far sooner
 constexpr int kFlatThreads = 256;
 
 __global__ void __launch_bounds__(kFlatThreads) k_flatten(int32_t* label, int64_t n) {
@@ -387,7 +387,7 @@ __global__ void __launch_bounds__(kFlatThreads) k_flatten(int32_t* label, int64_
         }
         // cached loads: a label read stale is still an ancestor of the
         // vertex (labels only decrease), so following it stays correct
-#pragma unroll
+#pragma unroll 1
         for (int h = 0; h < kFlatHops; ++h) {
             if (!__any_sync(0xffffffffu, open)) break;  // the warp's chains all ended
             int32_t w[kFlatPer];
@@ -400,9 +400,6 @@ __global__ void __launch_bounds__(kFlatThreads) k_flatten(int32_t* label, int64_
                     else r[j] = w[j];
                 }
         }
-#pragma unroll
-        for (int j = 0; j < kFlatPer; ++j)
-            if (open >> j & 1u) r[j] = find_g(label, r[j]);
 #pragma unroll
         for (int j = 0; j < kFlatPer; ++j) {
             const int64_t v = c * kChunk + (int64_t)j * kFlatThreads + threadIdx.x;
