@@ -522,7 +522,7 @@ def run_ours(args):
     stage_list.sort(key=lambda e: -e["share_of_step"])
     if roofline:
         roofline["stages"] = stage_list
-        roofline["north_star_kernels"] = {k: {kk: rooflines[k][kk] for kk in ("achieved", "frac", "avg_launch_ms")}
+        roofline["stencil_and_jumping"] = {k: {kk: rooflines[k][kk] for kk in ("achieved", "frac", "avg_launch_ms")}
                                           for k in ("steepest.grid", "compress.jump") if k in rooflines}
 
     out = {
