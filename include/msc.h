@@ -126,8 +126,8 @@ MSC_API int msc_steepest_csr(const int32_t* order, const int32_t* row, const int
  *        paper's -1 outside a feature mask) and are left as they are.
  *        An active entry pointing outside [0, n) or at an inactive entry
  *        sets MSC_ERR_ARG; a pointer cycle sets MSC_ERR_NOT_CONVERGED
- *        (every sweep advances each pointer by up to three hops; at most
- *        ceil(log4 n) + 2 sweeps are made). */
+ *        (every sweep advances each pointer by up to four hops; at most
+ *        ceil(log5 n) + 2 sweeps are made). */
 MSC_API int msc_compress(int32_t* ptr, int32_t n, void* ws, size_t ws_bytes, int32_t* d_status,
                  void* stream);
 
@@ -140,7 +140,7 @@ MSC_API int msc_compress(int32_t* ptr, int32_t n, void* ws, size_t ws_bytes, int
  * msc_compress does, with the same arguments minus the workspace, and
  * allocates nothing (no cudaMalloc, cudaFree or allocating library
  * routine).  It is an ordinary host call that enqueues work on `stream`
- * (a memset, an occupancy query and about log4(n) + 3 kernel launches), so
+ * (a memset, an occupancy query and about log5(n) + 3 kernel launches), so
  * it must not be made from a host function enqueued on a stream, where CUDA
  * calls are not allowed.
  *   n  at most MSC_NOALLOC_MAX_N; larger n returns MSC_ERR_TOO_LARGE.
