@@ -442,12 +442,14 @@ def run_ours(args):
         barrier()
         torch.cuda.synchronize()
         gc.disable()  # no collector pause while the host enqueues the steps
-        ev0.record(stream)
-        for j in range(ncs):
-            s_in[j].wait_event(ev0)
-        for i in range(ee):
-            e2e_step(i, timing=(ncs == 1))
-        gc.enable()
+        try:
+            ev0.record(stream)
+            for j in range(ncs):
+                s_in[j].wait_event(ev0)
+            for i in range(ee):
+                e2e_step(i, timing=(ncs == 1))
+        finally:
+            gc.enable()
         for b in range(2):
             for j in range(ncs):
                 stream.wait_event(ev_out[b][j])
